@@ -1,0 +1,546 @@
+/*
+ * FP64 oracle for the coupled flow + advection-diffusion lattice Boltzmann solvers of
+ * Tsompanas et al., "Modelling Microbial Fuel Cells using lattice Boltzmann methods"
+ * (arXiv 1802.07525), Sec. 3.1.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct CPU restatement of
+ * the method, used to check the CUDA path.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product library never links, calls or falls
+ * back to it.  It shares no code, header, table or constant with the CUDA path.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, round to nearest).
+ *
+ * Conventions (readings of the paper where it is silent or garbled are listed at each place):
+ *   - lattice units dx = dt = 1, rho0 = 1;
+ *   - node index k = x + nx*(y + ny*z) (x fastest);
+ *   - populations are SoA: f[i*N + k];
+ *   - the flow axis is x in 2-D and z in 3-D; the inlet is at the low end of that axis;
+ *   - node classes are bit flags: 1 = blocked for the flow lattice, 2 = blocked for the
+ *     transport lattice, 4 = consumption (sink) node.
+ *
+ * Parity status: every function here is pinned by the "not gpu" tests (closed forms,
+ * conservation laws, symmetry, published generator vectors); none is unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+enum { BC_WALL = 0, BC_PERIODIC = 1, BC_INOUT = 2 };
+enum { CLS_FLOW_SOLID = 1, CLS_ADE_SOLID = 2, CLS_SINK = 4 };
+enum { SRC_NODE = 0, SRC_BOUNCE = 1, SRC_INLET = 2, SRC_OUTLET = 3 };
+
+typedef struct {
+    int dim;           /* 2 or 3 */
+    int nx, ny, nz;    /* nz = 1 in 2-D */
+    int bc[3];         /* per axis: BC_WALL, BC_PERIODIC, BC_INOUT (flow axis only) */
+    int ade_q;         /* 5 (D2Q5), 7 (D3Q7) or 9 (D2Q9 with the Eq. 5 equilibrium) */
+    int ade_outlet;    /* 0 zero-gradient, 1 Dirichlet at c_out */
+    double tau;        /* flow relaxation time, Eq. 4 */
+    double tau_c;      /* transport relaxation time tau_D, Eq. 12 */
+    double u_in;       /* inlet speed along the flow axis */
+    double rho_in;     /* density of the moving wall that forms the flow inlet */
+    double rho_out;    /* outlet density (pressure reference) */
+    double c_in;       /* inlet concentration (Dirichlet input) */
+    double c_out;      /* outlet concentration when ade_outlet = 1 */
+    double k_sink;     /* first-order consumption rate on sink nodes */
+    double u_scale;    /* factor applied to the flow velocity seen by the transport solver */
+} orc_params;
+
+/* ------------------------------------------------------------------------------------------
+ * Velocity sets.
+ * D2Q9 follows Eqs. 1-3 with weights Eqs. 6-8.  The order of c5..c8 is fixed by the pairs of
+ * Eq. 11 (south wall: 5<->7, 2<->4, 6<->8), i.e. 5=(1,1), 6=(-1,1), 7=(-1,-1), 8=(1,-1).
+ * D3Q19 (flow, 3-D) and D2Q5 / D3Q7 (transport) are the standard sets; the paper only states
+ * that the 3-D extension is direct (Sec. 2) and gives no ordering, so opposites are adjacent.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int q;
+    const int (*c)[3];
+    const int *opp;
+    const double *w;
+    double cs2;
+} vset;
+
+static const int D2Q9_C[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+static const int D2Q9_OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double D2Q9_W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                                 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static const int D2Q5_C[5][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}};
+static const int D2Q5_OPP[5] = {0, 3, 4, 1, 2};
+static const double D2Q5_W[5] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+
+static const int D3Q19_C[19][3] = {
+    {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+static const int D3Q19_OPP[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+static const double D3Q19_W[19] = {
+    1.0 / 3.0,  1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static const int D3Q7_C[7][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},
+                                 {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+static const int D3Q7_OPP[7] = {0, 2, 1, 4, 3, 6, 5};
+static const double D3Q7_W[7] = {1.0 / 4.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0,
+                                 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0};
+
+static vset flow_set(const orc_params *p)
+{
+    vset v;
+    if (p->dim == 2) {
+        v.q = 9; v.c = D2Q9_C; v.opp = D2Q9_OPP; v.w = D2Q9_W;
+    } else {
+        v.q = 19; v.c = D3Q19_C; v.opp = D3Q19_OPP; v.w = D3Q19_W;
+    }
+    v.cs2 = 1.0 / 3.0;
+    return v;
+}
+
+static vset ade_set(const orc_params *p)
+{
+    vset v;
+    if (p->ade_q == 9) {
+        v.q = 9; v.c = D2Q9_C; v.opp = D2Q9_OPP; v.w = D2Q9_W; v.cs2 = 1.0 / 3.0;
+    } else if (p->ade_q == 7) {
+        v.q = 7; v.c = D3Q7_C; v.opp = D3Q7_OPP; v.w = D3Q7_W; v.cs2 = 1.0 / 4.0;
+    } else {
+        v.q = 5; v.c = D2Q5_C; v.opp = D2Q5_OPP; v.w = D2Q5_W; v.cs2 = 1.0 / 3.0;
+    }
+    return v;
+}
+
+static long n_nodes(const orc_params *p) { return (long)p->nx * p->ny * p->nz; }
+static int flow_axis(const orc_params *p) { return p->dim == 2 ? 0 : 2; }
+
+/* ------------------------------------------------------------------------------------------
+ * Equilibria.
+ * Flow, Eq. 5: F_i^(0) = w_i rho [1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 u.u].  The printed
+ * c = dx/(dt sqrt 3) would make the coefficients 9, 81/2, 9/2; the reading taken is the
+ * standard one (c = dx/dt = 1, sound speed squared 1/3), which Table 1 confirms: tau_D =
+ * 0.5036 and D = 0.0012 mm^2/s satisfy D = (tau_D - 1/2)/3 exactly.
+ * Transport, Eq. 12: on D2Q5 / D3Q7 the equilibrium is the linear one,
+ * G_i^(0) = w_i C (1 + c_i.u / cs2); on D2Q9 (ade_q = 9) it is Eq. 5 reused with C in
+ * place of rho, as the text after Eq. 12 says.
+ * ------------------------------------------------------------------------------------------ */
+static void flow_equilibrium(const vset *v, double rho, const double u[3], double *feq)
+{
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < v->q; ++i) {
+        double cu = v->c[i][0] * u[0] + v->c[i][1] * u[1] + v->c[i][2] * u[2];
+        feq[i] = v->w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+static void ade_equilibrium(const vset *v, double conc, const double u[3], double *geq)
+{
+    if (v->q == 9) {
+        flow_equilibrium(v, conc, u, geq);
+        return;
+    }
+    for (int i = 0; i < v->q; ++i) {
+        double cu = v->c[i][0] * u[0] + v->c[i][1] * u[1] + v->c[i][2] * u[2];
+        geq[i] = v->w[i] * conc * (1.0 + cu / v->cs2);
+    }
+}
+
+ORC_API void orc_flow_equilibrium(int dim, double rho, const double *u, double *feq)
+{
+    orc_params p;
+    memset(&p, 0, sizeof p);
+    p.dim = dim;
+    vset v = flow_set(&p);
+    double uu[3] = {u[0], u[1], dim == 3 ? u[2] : 0.0};
+    flow_equilibrium(&v, rho, uu, feq);
+}
+
+ORC_API void orc_ade_equilibrium(int ade_q, double conc, const double *u, double *geq)
+{
+    orc_params p;
+    memset(&p, 0, sizeof p);
+    p.ade_q = ade_q;
+    vset v = ade_set(&p);
+    double uu[3] = {u[0], u[1], ade_q == 7 ? u[2] : 0.0};
+    ade_equilibrium(&v, conc, uu, geq);
+}
+
+/* Velocity-set tables, for the isotropy pins. */
+ORC_API int orc_velocity_set(int which, int *c, int *opp, double *w)
+{
+    orc_params p;
+    memset(&p, 0, sizeof p);
+    vset v;
+    if (which == 9) { p.dim = 2; v = flow_set(&p); }
+    else if (which == 19) { p.dim = 3; v = flow_set(&p); }
+    else { p.ade_q = which; v = ade_set(&p); }
+    for (int i = 0; i < v.q; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = v.c[i][a];
+        opp[i] = v.opp[i];
+        w[i] = v.w[i];
+    }
+    return v.q;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Pull streaming with boundaries (Eq. 4 streaming part, Eq. 11 bounce-back).
+ * The population that arrives at x along c_i comes from s = x - c_i.
+ *   - s outside the lattice across a wall, or s blocked: half-way bounce-back, i.e. the
+ *     population that left x along the opposite direction returns (Eq. 11; the wall sits
+ *     half-way along the link, so a channel of NY nodes has width NY).
+ *   - s before the inlet (flow axis): SRC_INLET.  Flow: bounce-back from a wall moving at
+ *     the inlet velocity.  Transport: an equilibrium ghost at the inlet concentration.
+ *   - s past the outlet: SRC_OUTLET, with *src = s moved back onto the last layer (unless
+ *     that node is blocked, which gives bounce-back).  Flow: equilibrium ghost at the
+ *     outlet density with the velocity of that last-layer node (zero velocity gradient,
+ *     pressure reference).  Transport: a copy of that node's population (zero gradient), or
+ *     an equilibrium ghost at c_out when the outlet is Dirichlet.
+ * Precedence: wall or solid first, then inlet, then outlet.  Blocked nodes hold no
+ * populations and are not collided.
+ * ------------------------------------------------------------------------------------------ */
+static int pull_source(const orc_params *p, const uint8_t *cls, int blocked_bit, int x, int y,
+                       int z, const int c[3], long *src)
+{
+    int n[3] = {p->nx, p->ny, p->nz};
+    int s[3] = {x - c[0], y - c[1], z - c[2]};
+    int fa = flow_axis(p);
+    int inlet = 0, outlet = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] >= 0 && s[a] < n[a]) continue;
+        if (p->bc[a] == BC_PERIODIC) {
+            s[a] = (s[a] + n[a]) % n[a];
+        } else if (p->bc[a] == BC_INOUT && a == fa) {
+            if (s[a] < 0) inlet = 1; else outlet = 1;
+        } else {
+            return SRC_BOUNCE; /* a wall (an inlet/outlet on a cross axis is treated as a wall) */
+        }
+    }
+    if (inlet) return SRC_INLET;
+    if (outlet) s[fa] = n[fa] - 1;
+    long j = s[0] + (long)n[0] * (s[1] + (long)n[1] * s[2]);
+    if (cls[j] & blocked_bit) return SRC_BOUNCE;
+    *src = j;
+    return outlet ? SRC_OUTLET : SRC_NODE;
+}
+
+/* Flow outlet ghost: F_i^(0)(rho_out, u) with u the velocity of the post-collision
+ * populations at last-layer node s (collision conserves mass and momentum, so this is the
+ * velocity of that node's streamed populations of the previous step). */
+static double outlet_equilibrium(const vset *v, const orc_params *p, const double *f, long N,
+                                 long s, int i)
+{
+    double r = 0.0, j[3] = {0, 0, 0};
+    for (int m = 0; m < v->q; ++m) {
+        r += f[m * N + s];
+        for (int a = 0; a < 3; ++a) j[a] += v->c[m][a] * f[m * N + s];
+    }
+    double u[3] = {j[0] / r, j[1] / r, j[2] / r};
+    double feq[19];
+    flow_equilibrium(v, p->rho_out, u, feq);
+    return feq[i];
+}
+
+/* One flow step (Eq. 4 with Eq. 5, moments Eqs. 9-10, bounce-back Eq. 11).
+ * In:  f   = post-collision populations of the previous step.
+ * Out: fn  = post-collision populations of this step (0 on blocked nodes);
+ *      rho, u = moments of the streamed populations (before collision), 0 on blocked nodes. */
+ORC_API void orc_flow_step(const orc_params *p, const uint8_t *cls, const double *f, double *fn,
+                           double *rho, double *u)
+{
+    vset v = flow_set(p);
+    long N = n_nodes(p);
+    int fa = flow_axis(p);
+    double uin[3] = {0, 0, 0};
+    uin[fa] = p->u_in;
+    /* inlet: bounce-back from a wall moving at u_in (momentum-corrected bounce-back),
+     * F_i = F*_opp(i) + 2 w_i rho_in (c_i . u_in) / cs2, which injects exactly rho_in*u_in
+     * per unit of inlet cross-section */
+    double bb_in[19];
+    for (int i = 0; i < v.q; ++i) {
+        double cu = v.c[i][0] * uin[0] + v.c[i][1] * uin[1] + v.c[i][2] * uin[2];
+        bb_in[i] = 2.0 * v.w[i] * p->rho_in * cu / v.cs2;
+    }
+
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = x + (long)p->nx * (y + (long)p->ny * z);
+                if (cls[k] & CLS_FLOW_SOLID) {
+                    for (int i = 0; i < v.q; ++i) fn[i * N + k] = 0.0;
+                    rho[k] = 0.0;
+                    for (int a = 0; a < p->dim; ++a) u[a * N + k] = 0.0;
+                    continue;
+                }
+                double fin[19];
+                for (int i = 0; i < v.q; ++i) {
+                    long s;
+                    switch (pull_source(p, cls, CLS_FLOW_SOLID, x, y, z, v.c[i], &s)) {
+                    case SRC_NODE: fin[i] = f[i * N + s]; break;
+                    case SRC_BOUNCE: fin[i] = f[v.opp[i] * N + k]; break;
+                    case SRC_INLET: fin[i] = f[v.opp[i] * N + k] + bb_in[i]; break;
+                    default: fin[i] = outlet_equilibrium(&v, p, f, N, s, i); break;
+                    }
+                }
+                double r = 0.0, j[3] = {0, 0, 0};
+                for (int i = 0; i < v.q; ++i) {
+                    r += fin[i];
+                    for (int a = 0; a < 3; ++a) j[a] += v.c[i][a] * fin[i];
+                }
+                double uu[3] = {j[0] / r, j[1] / r, j[2] / r};
+                double feq[19];
+                flow_equilibrium(&v, r, uu, feq);
+                for (int i = 0; i < v.q; ++i) fn[i * N + k] = fin[i] - (fin[i] - feq[i]) / p->tau;
+                rho[k] = r;
+                for (int a = 0; a < p->dim; ++a) u[a * N + k] = uu[a];
+            }
+}
+
+/* One transport step (Eq. 12 with the consumption sink, concentration Eq. 13).
+ * The velocity u (dim x N) is held fixed during the transport solve (text after Eq. 12); it
+ * is scaled by u_scale and taken as zero on nodes blocked for the flow (biofilm is
+ * impermeable to flow, Sec. 3.3, but still takes part in transport).
+ * Consumption: the first-order rate k*C on sink nodes, removed in proportion to the weights,
+ * so that sum_i G_i loses exactly k*C per sink node per step.  Eq. 12 prints no source term;
+ * the consumption follows the substrate uptake of Eq. 16 in its first-order limit.
+ * Out: gn (0 on blocked nodes) and conc = moment of the streamed populations (Eq. 13). */
+ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double *g, double *gn,
+                          const double *u, double *conc)
+{
+    vset v = ade_set(p);
+    long N = n_nodes(p);
+    int fa = flow_axis(p);
+    double uin[3] = {0, 0, 0};
+    uin[fa] = p->u_in;
+    double geq_in[19], geq_out[19];
+    ade_equilibrium(&v, p->c_in, uin, geq_in);
+    ade_equilibrium(&v, p->c_out, uin, geq_out);
+
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = x + (long)p->nx * (y + (long)p->ny * z);
+                if (cls[k] & CLS_ADE_SOLID) {
+                    for (int i = 0; i < v.q; ++i) gn[i * N + k] = 0.0;
+                    conc[k] = 0.0;
+                    continue;
+                }
+                double uk[3] = {0, 0, 0};
+                if (!(cls[k] & CLS_FLOW_SOLID))
+                    for (int a = 0; a < p->dim; ++a) uk[a] = u[a * N + k] * p->u_scale;
+                double gin[19];
+                for (int i = 0; i < v.q; ++i) {
+                    long s;
+                    switch (pull_source(p, cls, CLS_ADE_SOLID, x, y, z, v.c[i], &s)) {
+                    case SRC_NODE: gin[i] = g[i * N + s]; break;
+                    case SRC_BOUNCE: gin[i] = g[v.opp[i] * N + k]; break;
+                    case SRC_INLET: gin[i] = geq_in[i]; break;
+                    default: gin[i] = p->ade_outlet == 1 ? geq_out[i] : g[i * N + s]; break;
+                    }
+                }
+                double C = 0.0;
+                for (int i = 0; i < v.q; ++i) C += gin[i];
+                double geq[19];
+                ade_equilibrium(&v, C, uk, geq);
+                double sink = (cls[k] & CLS_SINK) ? p->k_sink * C : 0.0;
+                for (int i = 0; i < v.q; ++i)
+                    gn[i * N + k] = gin[i] - (gin[i] - geq[i]) / p->tau_c - v.w[i] * sink;
+                conc[k] = C;
+            }
+}
+
+/* Global sums used by the steady-state test and the current (FP64).
+ * out[0] = sum |u - u_prev|^2, out[1] = sum |u|^2, out[2] = sum rho      (flow-active nodes)
+ * out[3] = sum (C - C_prev)^2, out[4] = sum C^2,  out[5] = sum C        (transport-active)
+ * out[6] = sum over sink nodes of k*C  (the consumption that sets the current, Eqs. 16, 20)
+ * out[7] = number of non-finite values met. */
+ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho, const double *u,
+                      const double *u_prev, const double *conc, const double *conc_prev,
+                      double *out)
+{
+    long N = n_nodes(p);
+    for (int m = 0; m < 8; ++m) out[m] = 0.0;
+    for (long k = 0; k < N; ++k) {
+        if (!(cls[k] & CLS_FLOW_SOLID) && rho) {
+            for (int a = 0; a < p->dim; ++a) {
+                double d = u[a * N + k] - u_prev[a * N + k];
+                out[0] += d * d;
+                out[1] += u[a * N + k] * u[a * N + k];
+                if (!isfinite(u[a * N + k])) out[7] += 1.0;
+            }
+            out[2] += rho[k];
+            if (!isfinite(rho[k])) out[7] += 1.0;
+        }
+        if (!(cls[k] & CLS_ADE_SOLID) && conc) {
+            double d = conc[k] - conc_prev[k];
+            out[3] += d * d;
+            out[4] += conc[k] * conc[k];
+            out[5] += conc[k];
+            if (cls[k] & CLS_SINK) out[6] += p->k_sink * conc[k];
+            if (!isfinite(conc[k])) out[7] += 1.0;
+        }
+    }
+}
+
+static double rel_residual(double d2, double n2)
+{
+    if (n2 > 0.0) return sqrt(d2 / n2);
+    return d2 > 0.0 ? INFINITY : 0.0;
+}
+
+/* Initial state (the paper is silent): flow at rest, F_i = w_i on open nodes; no substrate,
+ * G_i = 0 everywhere. */
+ORC_API void orc_init_state(const orc_params *p, const uint8_t *cls, double *f, double *g)
+{
+    vset vf = flow_set(p), va = ade_set(p);
+    long N = n_nodes(p);
+    for (long k = 0; k < N; ++k) {
+        for (int i = 0; i < vf.q; ++i) f[i * N + k] = (cls[k] & CLS_FLOW_SOLID) ? 0.0 : vf.w[i];
+        for (int i = 0; i < va.q; ++i) g[i * N + k] = 0.0;
+    }
+}
+
+enum { MODE_SEQUENTIAL = 0, MODE_CONCURRENT = 1 };
+
+typedef struct {
+    long steps_flow, steps_ade;
+    double res_flow, res_ade, current, mass, substrate;
+    int converged;
+} orc_result;
+
+/* Iterate to equilibrium (method steps 2 and 3 of Sec. 3; "enough time steps until an
+ * equilibrium is reached", Sec. 4).  The test is r = ||v^n - v^(n-1)|| / ||v^n|| < tol,
+ * evaluated at steps n that are multiples of check_every (1 = every step).
+ * SEQUENTIAL: the flow runs to equilibrium, then transport runs with that velocity frozen
+ * (the paper's order).  CONCURRENT: both advance together, transport using the same step's
+ * flow velocity; both residuals must fall below their tolerances.
+ * f, g: state in/out.  rho, u, conc: fields of the last step, out.  Returns converged. */
+ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f, double *g,
+                             double *rho, double *u, double *conc, int mode, double tol_flow,
+                             double tol_ade, long max_steps, int check_every, orc_result *res)
+{
+    vset vf = flow_set(p), va = ade_set(p);
+    long N = n_nodes(p);
+    int d = p->dim;
+    double *f2 = calloc((size_t)vf.q * N, sizeof(double));
+    double *g2 = calloc((size_t)va.q * N, sizeof(double));
+    double *u_prev = calloc((size_t)d * N, sizeof(double));
+    double *c_prev = calloc((size_t)N, sizeof(double));
+    double s[8];
+    memset(res, 0, sizeof *res);
+    int conv_f = 0, conv_a = 0;
+    if (check_every < 1) check_every = 1;
+
+    if (mode == MODE_SEQUENTIAL) {
+        for (long n = 1; n <= max_steps; ++n) {
+            memcpy(u_prev, u, sizeof(double) * d * N);
+            orc_flow_step(p, cls, f, f2, rho, u);
+            memcpy(f, f2, sizeof(double) * vf.q * N);
+            res->steps_flow = n;
+            if (n % check_every == 0) {
+                orc_sums(p, cls, rho, u, u_prev, NULL, NULL, s);
+                res->res_flow = rel_residual(s[0], s[1]);
+                res->mass = s[2];
+                if (res->res_flow < tol_flow) { conv_f = 1; break; }
+            }
+        }
+        for (long n = 1; n <= max_steps; ++n) {
+            memcpy(c_prev, conc, sizeof(double) * N);
+            orc_ade_step(p, cls, g, g2, u, conc);
+            memcpy(g, g2, sizeof(double) * va.q * N);
+            res->steps_ade = n;
+            if (n % check_every == 0) {
+                orc_sums(p, cls, NULL, u, u, conc, c_prev, s);
+                res->res_ade = rel_residual(s[3], s[4]);
+                res->substrate = s[5];
+                res->current = s[6];
+                if (res->res_ade < tol_ade) { conv_a = 1; break; }
+            }
+        }
+    } else {
+        for (long n = 1; n <= max_steps; ++n) {
+            memcpy(u_prev, u, sizeof(double) * d * N);
+            memcpy(c_prev, conc, sizeof(double) * N);
+            orc_flow_step(p, cls, f, f2, rho, u);
+            orc_ade_step(p, cls, g, g2, u, conc);
+            memcpy(f, f2, sizeof(double) * vf.q * N);
+            memcpy(g, g2, sizeof(double) * va.q * N);
+            res->steps_flow = res->steps_ade = n;
+            if (n % check_every == 0) {
+                orc_sums(p, cls, rho, u, u_prev, conc, c_prev, s);
+                res->res_flow = rel_residual(s[0], s[1]);
+                res->res_ade = rel_residual(s[3], s[4]);
+                res->mass = s[2];
+                res->substrate = s[5];
+                res->current = s[6];
+                if (res->res_flow < tol_flow && res->res_ade < tol_ade) {
+                    conv_f = conv_a = 1;
+                    break;
+                }
+            }
+        }
+    }
+    res->converged = conv_f && conv_a;
+    free(f2); free(g2); free(u_prev); free(c_prev);
+    return res->converged;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Biofilm growth rule of the 2048x1024 cycle workload (a simplified stand-in for the agent
+ * model of Sec. 3.3): an open node (no class bit set) becomes biofilm when one of its
+ * flow-lattice neighbours is a consumption node, its concentration is above c_thresh
+ * (strictly), and a uniform draw is below prob.  New biofilm is impermeable to flow and
+ * consumes substrate (Sec. 3.3: "the updated biofilm as impermeable"), i.e. class
+ * CLS_FLOW_SOLID | CLS_SINK.  All decisions read the classes from before the pass.
+ * Neighbours are the non-rest directions of the flow velocity set, inside the lattice only.
+ * Draw: h = splitmix64(seed ^ (cycle << 32) ^ k); convert when (h >> 11) < prob * 2^53.
+ * splitmix64 is Steele, Lea and Flood's generator (OOPSLA 2014) as published by Vigna:
+ * z = x + 0x9e3779b97f4a7c15; z = (z ^ z>>30) * 0xbf58476d1ce4e5b9;
+ * z = (z ^ z>>27) * 0x94d049bb133111eb; return z ^ z>>31.
+ * Returns the number of converted nodes.
+ * ------------------------------------------------------------------------------------------ */
+ORC_API uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+ORC_API long orc_biofilm_convert(const orc_params *p, const uint8_t *cls, const double *conc,
+                                 uint64_t seed, uint64_t cycle, double prob, double c_thresh,
+                                 uint8_t *cls_out)
+{
+    vset v = flow_set(p);
+    long N = n_nodes(p);
+    double lim = floor(prob * 9007199254740992.0); /* prob * 2^53 */
+    long count = 0;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = x + (long)p->nx * (y + (long)p->ny * z);
+                cls_out[k] = cls[k];
+                if (cls[k] != 0) continue;
+                int near = 0;
+                for (int i = 1; i < v.q && !near; ++i) {
+                    int sx = x + v.c[i][0], sy = y + v.c[i][1], sz = z + v.c[i][2];
+                    if (sx < 0 || sx >= p->nx || sy < 0 || sy >= p->ny || sz < 0 || sz >= p->nz)
+                        continue;
+                    long j = sx + (long)p->nx * (sy + (long)p->ny * sz);
+                    if (cls[j] & CLS_SINK) near = 1;
+                }
+                if (!near || !(conc[k] > c_thresh)) continue;
+                uint64_t h = orc_splitmix64(seed ^ (cycle << 32) ^ (uint64_t)k);
+                if ((double)(h >> 11) < lim) {
+                    cls_out[k] = CLS_FLOW_SOLID | CLS_SINK;
+                    ++count;
+                }
+            }
+    return count;
+}
+
+ORC_API int orc_params_size(void) { return (int)sizeof(orc_params); }
+ORC_API int orc_result_size(void) { return (int)sizeof(orc_result); }
