@@ -1,0 +1,197 @@
+/*
+ * mfc.h — C ABI of the GB300 (sm_103a) library for the coupled flow + substrate-transport
+ * lattice Boltzmann solvers of the microbial fuel cell model of Tsompanas et al.,
+ * "Modelling Microbial Fuel Cells using lattice Boltzmann methods" (arXiv 1802.07525).
+ *
+ * What the library computes (Sec. 3 of the paper, steps 2 and 3 of the model loop):
+ *   - flow: BGK lattice Boltzmann (Eq. 4) with the equilibrium of Eq. 5, moments Eqs. 9-10 and
+ *     half-way bounce-back on walls, electrode and biofilm (Eq. 11); D2Q9 in 2-D, D3Q19 in 3-D;
+ *   - transport: BGK advection-diffusion lattice Boltzmann (Eq. 12, concentration Eq. 13) of
+ *     the substrate, driven by the flow velocity, zero flux on solids, Dirichlet inlet;
+ *     D2Q5 / D3Q7; a first-order consumption k*C on biofilm (sink) nodes;
+ *   - the consumption summed over the lattice (the current of the anode in lattice units,
+ *     the chain of Eqs. 16 and 20), and the residuals that decide steady state.
+ *
+ * Conventions shared by every call:
+ *   - Lattice units: dx = dt = 1, reference density 1.  The flow axis is x in 2-D and z in 3-D;
+ *     the inlet is at its low end.
+ *   - Node order: x fastest, then y, then z; N = nx*ny*nz.  Host arrays are dense in this order.
+ *   - Node classes (uint8 per node): bit 0 (1) blocked for the flow, bit 1 (2) blocked for
+ *     transport, bit 2 (4) consumption node.  Electrode = 3, biofilm next to electrode = 4
+ *     (consumes, open to flow) or 5 (consumes, impermeable to flow).
+ *   - Boundary kinds per axis: MFC_BC_WALL (half-way bounce-back walls outside the first and
+ *     last layer), MFC_BC_PERIODIC, MFC_BC_INOUT (flow axis only: moving-wall bounce-back
+ *     inlet at u_in; outlet at density rho_out with the velocity of the last layer; transport
+ *     inlet at c_in, zero-gradient or Dirichlet-c_out outlet).
+ *   - Ownership: the library allocates and owns all device memory of a lattice; every host
+ *     pointer belongs to the caller and is only read or written during the call.
+ *   - Streams: a lattice runs on the stream given in its descriptor (NULL: a stream the
+ *     library creates).  Stepping calls are asynchronous on that stream; read calls and
+ *     mfc_solve_steady block until their results are on the host.
+ *   - Errors: every call returns an mfc_status; nothing aborts or exits.  A CUDA error is
+ *     recorded on the lattice and returned by that call and every later call on it.
+ *   - Precision: populations are stored as deviations from the rest state (f_i - w_i and
+ *     g_i - w_i*c_in), in FP32 (MFC_FP32) or FP16 (MFC_FP16_DEV); arithmetic is FP32;
+ *     residual, mass and current sums are FP64.
+ */
+#ifndef MFC_H
+#define MFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MFC_API __attribute__((visibility("default")))
+#else
+#define MFC_API
+#endif
+
+typedef struct mfc_lattice mfc_lattice; /* opaque; owns its device memory */
+
+typedef enum {
+    MFC_OK = 0,
+    MFC_ERR_ARG = 1,          /* invalid argument (size, pointer, parameter range) */
+    MFC_ERR_OOM = 2,          /* device allocation failed */
+    MFC_ERR_OOM_BUDGET = 3,   /* the request does not fit the memory budget of a batch */
+    MFC_ERR_CUDA = 4,         /* a CUDA call failed; see mfc_last_error */
+    MFC_NOT_CONVERGED = 5,    /* step cap reached before the residuals fell below tolerance */
+    MFC_ERR_NONFINITE = 6,    /* a residual, mass or current sum was not finite */
+    MFC_ERR_TIMEOUT = 7,      /* the host-side wall-clock limit of a solve was reached */
+    MFC_ERR_STATE = 8         /* call not valid in the object's current state */
+} mfc_status;
+
+enum { MFC_BC_WALL = 0, MFC_BC_PERIODIC = 1, MFC_BC_INOUT = 2 };
+enum { MFC_FP32 = 0, MFC_FP16_DEV = 1 };
+enum { MFC_SEQUENTIAL = 0, MFC_CONCURRENT = 1 };
+enum { MFC_OUTLET_ZERO_GRADIENT = 0, MFC_OUTLET_DIRICHLET = 1 };
+enum { MFC_POP_FLOW = 0, MFC_POP_ADE = 1, MFC_FIELD_VELOCITY = 2 };
+
+typedef struct {
+    int dim;          /* 2 or 3 */
+    int nx, ny, nz;   /* lattice size; nz = 1 in 2-D */
+    int bc[3];        /* boundary kind per axis */
+    int precision;    /* MFC_FP32 or MFC_FP16_DEV (population storage) */
+    void *stream;     /* cudaStream_t, or NULL for a library-owned stream */
+} mfc_lattice_desc;
+
+typedef struct {
+    double tau;        /* flow relaxation time (Eq. 4), > 0.5; viscosity (tau - 1/2)/3 */
+    double tau_c;      /* transport relaxation time tau_D (Eq. 12), > 0.5 */
+    double u_in;       /* inlet speed along the flow axis */
+    double rho_in;     /* density of the moving wall forming the inlet (normally 1) */
+    double rho_out;    /* outlet density (pressure reference, normally 1) */
+    double c_in;       /* inlet substrate concentration */
+    double c_out;      /* outlet concentration for a Dirichlet outlet */
+    double k_sink;     /* first-order consumption rate on sink nodes, in [0, 1) */
+    double u_scale;    /* factor on the flow velocity seen by transport (1 = same units) */
+    int ade_outlet;    /* MFC_OUTLET_ZERO_GRADIENT or MFC_OUTLET_DIRICHLET */
+} mfc_params;
+
+typedef struct {
+    double tol_flow;   /* flow steady when ||u^n - u^(n-1)|| / ||u^n|| < tol_flow */
+    double tol_ade;    /* transport steady when ||C^n - C^(n-1)|| / ||C^n|| < tol_ade */
+    long max_steps;    /* step cap per solver (sequential) or for both (concurrent) */
+    int check_every;   /* K: residual test every K steps (rounded up to an even number) */
+    int mode;          /* MFC_SEQUENTIAL (flow to steady, then transport) or MFC_CONCURRENT */
+    double timeout_s;  /* host wall-clock limit; <= 0 for none */
+} mfc_solve_opts;
+
+typedef struct {
+    long steps_flow, steps_ade; /* steps taken by each solver in this call */
+    double res_flow, res_ade;   /* residuals at the last check */
+    double current;             /* sum over consumption nodes of k*C at the last check */
+    double mass;                /* sum of rho over flow-open nodes at the last check */
+    double substrate;           /* sum of C over transport-open nodes at the last check */
+    int status;                 /* the mfc_status the call returned */
+} mfc_solve_result;
+
+/* ---- lattice life cycle ---------------------------------------------------------------- */
+
+/* Allocate a lattice (populations A/B, classes, link masks, fields, reduction scratch) on the
+ * current CUDA device.  Fails with MFC_ERR_ARG for bad sizes/kinds, tau or tau_c <= 0.5,
+ * an INOUT kind on a cross axis; MFC_ERR_OOM when device memory is short.  The lattice
+ * starts with every node open and the rest state (flow at rest, no substrate). */
+MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_params *params,
+                                      mfc_lattice **out);
+MFC_API mfc_status mfc_destroy_lattice(mfc_lattice *lat);
+
+/* Replace the physical parameters (relaxation times, inlet, consumption rate, ...). */
+MFC_API mfc_status mfc_set_params(mfc_lattice *lat, const mfc_params *params);
+
+/* Copy N node classes from host memory and rebuild the link masks (Eq. 11 decides which
+ * links bounce back).  reset_fields != 0: every open node returns to the rest state.
+ * reset_fields == 0: populations are kept (warm start); nodes that open up start at rest,
+ * nodes that become blocked drop their populations.  Class values above 7 are rejected. */
+MFC_API mfc_status mfc_set_geometry(mfc_lattice *lat, const uint8_t *node_class,
+                                    int reset_fields);
+
+/* ---- stepping (asynchronous on the lattice stream) ------------------------------------- */
+
+/* nsteps flow steps (Eq. 4).  The last one stores rho and u in the field buffers. */
+MFC_API mfc_status mfc_step_flow(mfc_lattice *lat, int nsteps);
+/* nsteps transport steps (Eq. 12) with the stored velocity held fixed (the paper's order).
+ * The last one stores C. */
+MFC_API mfc_status mfc_step_ade(mfc_lattice *lat, int nsteps);
+/* nsteps fused steps of both lattices; transport uses the same step's flow velocity. */
+MFC_API mfc_status mfc_step_coupled(mfc_lattice *lat, int nsteps);
+
+/* Iterate to steady state (Sec. 4: "enough time steps until an equilibrium is reached"),
+ * checking the residuals every K steps with CUDA-graph replays of K steps.  Blocks.
+ * Returns MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_NONFINITE or MFC_ERR_TIMEOUT; out (optional)
+ * is filled in every case. */
+MFC_API mfc_status mfc_solve_steady(mfc_lattice *lat, const mfc_solve_opts *opts,
+                                    mfc_solve_result *out);
+
+/* ---- biofilm growth between steady solves ---------------------------------------------- */
+
+/* Grow biofilm: every open node (class 0) with a consumption node among its flow-lattice
+ * neighbours, local concentration C > c_thresh and a draw below prob becomes impermeable
+ * biofilm (class 5).  Draw: splitmix64(seed ^ (cycle << 32) ^ node), converted when its top
+ * 53 bits are below prob * 2^53.  Decisions read the classes from before the pass and the
+ * concentration field of the last stepping call.  The link masks are rebuilt (warm start).
+ * n_converted (optional, host) receives the count; it blocks for that copy.  This is a
+ * simplified stand-in for the agent-based biofilm model of Sec. 3.3. */
+MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *lat, uint64_t seed, uint64_t cycle,
+                                    double prob, double c_thresh, long *n_converted);
+
+/* ---- reading results and checkpointing (blocking) --------------------------------------- */
+
+/* Fields of the last stepping call, as doubles in host memory (each pointer may be NULL):
+ * rho[N] (flow moment Eq. 9, 0 on flow-blocked nodes), u[dim*N] (component-major, Eq. 10,
+ * 0 on flow-blocked nodes), c[N] (Eq. 13, 0 on transport-blocked nodes), current[1] (sum of
+ * k*C over consumption nodes at the last residual check or solve). */
+MFC_API mfc_status mfc_read_fields(mfc_lattice *lat, double *rho, double *u, double *c,
+                                   double *current);
+
+/* Raw populations for checkpoint/resume and parity checks, as absolute values in doubles:
+ * which = MFC_POP_FLOW (Q_flow*N, direction-major), MFC_POP_ADE (Q_ade*N), or
+ * MFC_FIELD_VELOCITY (dim*N, the velocity that transport steps read).  Blocked nodes read 0. */
+MFC_API mfc_status mfc_read_populations(mfc_lattice *lat, int which, double *host);
+MFC_API mfc_status mfc_write_populations(mfc_lattice *lat, int which, const double *host);
+
+/* Wait for all work queued on the lattice stream. */
+MFC_API mfc_status mfc_synchronize(mfc_lattice *lat);
+
+/* ---- introspection --------------------------------------------------------------------- */
+
+/* Number of nodes open for flow and for transport (computed at mfc_set_geometry). */
+MFC_API mfc_status mfc_active_nodes(mfc_lattice *lat, long *flow_open, long *ade_open);
+/* Bytes of device memory the lattice holds. */
+MFC_API mfc_status mfc_device_bytes(mfc_lattice *lat, size_t *bytes);
+/* Device memory a lattice with this descriptor would allocate (for admission control). */
+MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc);
+MFC_API const char *mfc_status_string(mfc_status s);
+/* Text of the last error recorded on the lattice (or of the last create failure when lat is
+ * NULL); the pointer stays valid until the next call on that lattice. */
+MFC_API const char *mfc_last_error(mfc_lattice *lat);
+/* Library version, e.g. "mfc 0.1 sm_103a". */
+MFC_API const char *mfc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFC_H */

@@ -1,0 +1,230 @@
+// Reduction finalize, link-mask construction, dense conversion and biofilm growth kernels
+// (included by the runtime only).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace mfc {
+
+// Add the per-block partials in a fixed order; write the sums and the residuals.
+__global__ void __launch_bounds__(256) finalize_kernel(const double *partials, int nblocks,
+                                                        double *results)
+{
+    __shared__ double sh[256][NSUM];
+    double acc[NSUM];
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) acc[m] += partials[(size_t)b * NSUM + m];
+    }
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) sh[threadIdx.x][m] = acc[m];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int m = 0; m < NSUM; ++m) sh[threadIdx.x][m] += sh[threadIdx.x + s][m];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double r[NSUM];
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) {
+            r[m] = sh[0][m];
+            results[m] = r[m];
+        }
+        results[RES_FLOW] = r[SUM_U2] > 0.0 ? sqrt(r[SUM_DU2] / r[SUM_U2])
+                                            : (r[SUM_DU2] > 0.0 ? INFINITY : 0.0);
+        results[RES_ADE] = r[SUM_C2] > 0.0 ? sqrt(r[SUM_DC2] / r[SUM_C2])
+                                           : (r[SUM_DC2] > 0.0 ? INFINITY : 0.0);
+    }
+}
+
+// ---- geometry ------------------------------------------------------------------------------
+
+
+
+// Is the link that brings a population along (cx,cy,cz) to (x,y,z) blocked?  Walls win over the
+// inlet and outlet; an outlet source is moved back onto the last layer, whose class decides.
+template <int DIM>
+__device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, int z, int cx, int cy,
+                                             int cz, uint8_t bit)
+{
+    int s[3] = {x - cx, y - cy, z - cz};
+    const int n[3] = {m.nx, m.ny, m.nz};
+    constexpr int FA = DIM == 2 ? 0 : 2;
+    for (int ax = 0; ax < DIM; ++ax) {
+        const bool out = s[ax] < 0 || s[ax] >= n[ax];
+        if (out && !(m.bc[ax] == BC_PERIODIC || (m.bc[ax] == BC_INOUT && ax == FA))) return true;
+    }
+    for (int ax = 0; ax < DIM; ++ax) {
+        if (s[ax] >= 0 && s[ax] < n[ax]) continue;
+        if (m.bc[ax] == BC_PERIODIC) {
+            s[ax] = s[ax] < 0 ? s[ax] + n[ax] : s[ax] - n[ax];
+        } else {
+            if (s[ax] < 0) return false;  // inlet ghost
+            s[ax] = n[ax] - 1;            // outlet: the last layer decides
+        }
+    }
+    return (m.cls_new[s[0] + (long long)m.nx * (s[1] + (long long)m.ny * s[2])] & bit) != 0;
+}
+
+template <int DIM> __global__ void build_links_kernel(const MaskArgs m)
+{
+    using F = FlowSet<DIM>;
+    using A = AdeSet<DIM>;
+    using LK = Links<DIM>;
+    using LinkT = typename LK::T;
+    const long long N = (long long)m.nx * m.ny * m.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % m.nx);
+        const int y = (int)((q / m.nx) % m.ny);
+        const int z = (int)(q / ((long long)m.nx * m.ny));
+        const long long k = x + (long long)m.px * (y + (long long)m.ny * z);
+        const uint8_t c = m.cls_new[q];
+        uint32_t L = 0;
+        if (c & CLS_FLOW) L |= 1u << LK::FLOW_SELF;
+        if (c & CLS_ADE) L |= 1u << LK::ADE_SELF;
+        if (c & CLS_SINK) L |= 1u << LK::SINK;
+        for (int i = 1; i < F::Q; ++i) {
+            if (mask_blocked<DIM>(m, x, y, z, F::c(i, 0), F::c(i, 1), F::c(i, 2), CLS_FLOW))
+                L |= 1u << i;
+        }
+        for (int i = 1; i < A::Q; ++i) {
+            if (mask_blocked<DIM>(m, x, y, z, A::c(i, 0), A::c(i, 1), A::c(i, 2), CLS_ADE))
+                L |= 1u << (LK::ADE_SELF + i);
+        }
+        reinterpret_cast<LinkT *>(m.link)[k] = (LinkT)L;
+
+        const uint8_t o = m.reset ? (uint8_t)(CLS_FLOW | CLS_ADE) : m.cls_old[q];
+        const bool f_open = !(c & CLS_FLOW), a_open = !(c & CLS_ADE);
+        if (f_open && (o & CLS_FLOW)) {  // opens up (or reset): flow at rest
+            for (int i = 0; i < F::Q; ++i) {
+                if (m.half) reinterpret_cast<__half *>(m.fpop)[i * m.plane + k] = __float2half_rn(0.f);
+                else reinterpret_cast<float *>(m.fpop)[i * m.plane + k] = 0.f;
+            }
+        }
+        if (a_open && (o & CLS_ADE)) {  // opens up (or reset): no substrate
+            for (int i = 0; i < A::Q; ++i) {
+                const float v = -A::w(i) * m.c_ref;
+                if (m.half) reinterpret_cast<__half *>(m.gpop)[i * m.plane + k] = __float2half_rn(v);
+                else reinterpret_cast<float *>(m.gpop)[i * m.plane + k] = v;
+            }
+        }
+        if (m.reset || !f_open) {
+            m.fld_rho[k] = 0.f;
+            for (int ax = 0; ax < DIM; ++ax) m.fld_u[ax * m.plane + k] = 0.f;
+        }
+        if (m.reset || !a_open) m.fld_c[k] = -m.c_ref;
+        if (f_open) atomicAdd(&m.counts[0], 1ull);
+        if (a_open) atomicAdd(&m.counts[1], 1ull);
+    }
+}
+
+// ---- fields and populations to and from dense FP64 ------------------------------------------
+
+
+
+__device__ __forceinline__ uint32_t read_link(const void *p, int is32, long long k)
+{
+    return is32 ? reinterpret_cast<const uint32_t *>(p)[k] : reinterpret_cast<const uint16_t *>(p)[k];
+}
+
+__global__ void fields_to_dense_kernel(const ConvArgs a)
+{
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % a.nx);
+        const long long r = q / a.nx;
+        const long long k = x + (long long)a.px * r;
+        const uint32_t L = read_link(a.link, a.link32, k);
+        const bool fo = !(L & (1u << a.flow_self)), ao = !(L & (1u << a.ade_self));
+        if (a.rho) a.rho[q] = fo ? 1.0 + (double)a.fld_rho[k] : 0.0;
+        if (a.u)
+            for (int ax = 0; ax < a.dim; ++ax)
+                a.u[ax * N + q] = fo ? (double)a.fld_u[ax * a.plane + k] : 0.0;
+        if (a.c) a.c[q] = ao ? (double)(a.c_ref + a.fld_c[k]) : 0.0;
+    }
+}
+
+
+
+__global__ void pop_convert_kernel(const PopArgs a)
+{
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % a.nx);
+        const long long k = x + (long long)a.px * (q / a.nx);
+        const bool open = a.self_bit < 0 || !(read_link(a.link, a.link32, k) & (1u << a.self_bit));
+        for (int i = 0; i < a.q; ++i) {
+            const long long p = i * a.plane + k;
+            if (a.to_dense) {
+                double v = 0.0;
+                if (open) {
+                    const float dv = a.half ? __half2float(reinterpret_cast<const __half *>(a.pop)[p])
+                                            : reinterpret_cast<const float *>(a.pop)[p];
+                    v = (double)dv + (double)a.w[i] * (double)a.offset;
+                }
+                a.dense[i * N + q] = v;
+            } else {
+                const float dv = (float)(a.dense[i * N + q] - (double)a.w[i] * (double)a.offset);
+                if (a.half) reinterpret_cast<__half *>(a.pop)[p] = __float2half_rn(dv);
+                else reinterpret_cast<float *>(a.pop)[p] = dv;
+            }
+        }
+    }
+}
+
+// ---- biofilm growth (simplified stand-in for the agent model of Sec. 3.3) --------------------
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+
+
+template <int DIM> __global__ void biofilm_grow_kernel(const GrowArgs g)
+{
+    using F = FlowSet<DIM>;
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const uint8_t c = g.cls[q];
+        uint8_t out = c;
+        if (c == 0) {
+            const int x = (int)(q % g.nx);
+            const int y = (int)((q / g.nx) % g.ny);
+            const int z = (int)(q / ((long long)g.nx * g.ny));
+            bool near = false;
+#pragma unroll
+            for (int i = 1; i < F::Q; ++i) {
+                const int sx = x + F::c(i, 0), sy = y + F::c(i, 1), sz = z + F::c(i, 2);
+                if (sx < 0 || sx >= g.nx || sy < 0 || sy >= g.ny || sz < 0 || sz >= g.nz) continue;
+                if (g.cls[sx + (long long)g.nx * (sy + (long long)g.ny * sz)] & CLS_SINK) near = true;
+            }
+            if (near) {
+                const long long k = x + (long long)g.px * (y + (long long)g.ny * z);
+                const float C = g.c_ref + g.fld_c[k];
+                if ((double)C > g.c_thresh) {
+                    const uint64_t h = splitmix64(g.seed ^ (g.cycle << 32) ^ (uint64_t)q);
+                    if ((h >> 11) < g.lim) {
+                        out = CLS_FLOW | CLS_SINK;
+                        atomicAdd(g.count, 1ull);
+                    }
+                }
+            }
+        }
+        g.cls_out[q] = out;
+    }
+}
+
+}  // namespace mfc

@@ -1,0 +1,117 @@
+// Velocity sets, link-mask layout and population storage of the sm_103a lattice Boltzmann
+// kernels (Tsompanas et al., arXiv 1802.07525, Sec. 3.1).
+//
+// D2Q9 follows Eqs. 1-3 and the weights of Eqs. 6-8; the order of c5..c8 is the one fixed by the
+// bounce-back pairs of Eq. 11 (5<->7, 2<->4, 6<->8).  D3Q19 (3-D flow) has the rest velocity, six
+// faces and twelve edges with opposites adjacent; D2Q5 / D3Q7 carry the substrate (Eq. 12).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace mfc {
+
+enum : int { BC_WALL = 0, BC_PERIODIC = 1, BC_INOUT = 2 };
+enum : uint8_t { CLS_FLOW = 1, CLS_ADE = 2, CLS_SINK = 4 };
+
+// ---- velocity sets ---------------------------------------------------------------------------
+
+template <int DIM> struct FlowSet;
+template <int DIM> struct AdeSet;
+
+template <> struct FlowSet<2> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        return t[i];
+    }
+    __host__ __device__ static constexpr float w(int i)
+    {
+        return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+    }
+};
+
+template <> struct FlowSet<3> {
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+    __host__ __device__ static constexpr float w(int i)
+    {
+        return i == 0 ? 1.0f / 3.0f : (i < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+};
+
+template <> struct AdeSet<2> {
+    static constexpr int Q = 5;
+    static constexpr float inv_cs2 = 3.0f;  // D = (tau_c - 1/2) / 3
+    __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<2>::c(i, a); }
+    __host__ __device__ static constexpr int opp(int i) { return FlowSet<2>::opp(i); }
+    __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 3.0f : 1.0f / 6.0f; }
+};
+
+template <> struct AdeSet<3> {
+    static constexpr int Q = 7;
+    static constexpr float inv_cs2 = 4.0f;  // D = (tau_c - 1/2) / 4
+    __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<3>::c(i, a); }
+    __host__ __device__ static constexpr int opp(int i) { return FlowSet<3>::opp(i); }
+    __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 4.0f : 1.0f / 8.0f; }
+};
+
+// ---- link masks ------------------------------------------------------------------------------
+// One word per node.  Bit 0: the node is blocked for the flow.  Bit i (1..Qf-1): the flow
+// population arriving along c_i bounces back (its source is a wall or a blocked node).
+// Bit Qf: blocked for transport.  Bit Qf+i (1..Qa-1): the transport population along c_i
+// bounces back.  Bit Qf+Qa: consumption node.
+template <int DIM> struct Links {
+    static constexpr int QF = FlowSet<DIM>::Q;
+    static constexpr int QA = AdeSet<DIM>::Q;
+    static constexpr int FLOW_SELF = 0;
+    static constexpr int ADE_SELF = QF;
+    static constexpr int SINK = QF + QA;
+    using T = typename std::conditional<(QF + QA < 16), uint16_t, uint32_t>::type;
+};
+
+// ---- storage ---------------------------------------------------------------------------------
+// Populations are stored as deviations from the rest state in FP32 or FP16; arithmetic is FP32.
+__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+
+// Sums produced by a residual-check step (one double each, per block then per lattice).
+enum : int {
+    SUM_DU2 = 0,    // sum |u^n - u^(n-1)|^2 over flow-open nodes
+    SUM_U2 = 1,     // sum |u^n|^2
+    SUM_MASS = 2,   // sum rho
+    SUM_DC2 = 3,    // sum (C^n - C^(n-1))^2 over transport-open nodes
+    SUM_C2 = 4,     // sum C^2
+    SUM_C = 5,      // sum C
+    SUM_CURRENT = 6,// sum over consumption nodes of k C
+    SUM_BAD = 7,    // count of non-finite values
+    NSUM = 8
+};
+
+// Per-lattice results written by the finalize kernel: the sums, then the two residuals.
+enum : int { RES_FLOW = NSUM, RES_ADE = NSUM + 1, NRESULT = NSUM + 2 };
+
+}  // namespace mfc

@@ -1,0 +1,42 @@
+// Host-side declarations shared by the runtime and the per-dimension kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_kernels.cuh"
+
+namespace mfc {
+
+enum : int { KIND_COUPLED = 0, KIND_FLOW = 1, KIND_ADE = 2 };
+
+// Everything a step launch needs, independent of dimension and storage type.
+struct StepHost {
+    int dim, half;
+    int kind, mode;
+    int nx, ny, nz, px;
+    long long plane;
+    int bc_flow_axis;
+    dim3 grid, block;
+    int rows_per_block;
+    const void *fsrc;
+    void *fdst;
+    const void *gsrc;
+    void *gdst;
+    const void *link;
+    float *fld_rho, *fld_u, *fld_c;
+    double *partials;
+    float omega, omega_c, k_sink, u_scale, rho_out, c_ref;
+    int ade_dirichlet;
+    float bb_in[19], gin_dev[7], gout_dev[7];
+};
+
+cudaError_t launch_step_2d(const StepHost &h, cudaStream_t s);
+cudaError_t launch_step_3d(const StepHost &h, cudaStream_t s);
+cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s);
+cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s);
+cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s);
+cudaError_t launch_fields_to_dense(const ConvArgs &a, cudaStream_t s);
+cudaError_t launch_pop_convert(const PopArgs &a, cudaStream_t s);
+
+}  // namespace mfc

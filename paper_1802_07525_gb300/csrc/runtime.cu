@@ -1,0 +1,857 @@
+// Lattice objects, memory, CUDA-graph step loops and the C ABI declared in include/mfc.h.
+//
+// A lattice owns, on one GPU: two buffers of flow populations and two of transport populations
+// (pull scheme: read one, write the other), one link word per node, the node classes, the
+// FP32 fields (rho - 1, u, C - c_ref) written on check steps, per-block FP64 partial sums and
+// the finalized results (mirrored into pinned host memory).  Steady solves replay a captured
+// CUDA graph of K steps (K-2 plain, one that stores the fields, one that compares against them
+// and reduces), then read the residuals from the pinned mirror.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mfc.h"
+#include "lbm_aux.cuh"
+#include "mfc_internal.h"
+
+namespace mfc {
+
+cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s)
+{
+    const long long N = (long long)m.nx * m.ny * m.nz;
+    const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
+    if (dim == 2) build_links_kernel<2><<<blocks, 256, 0, s>>>(m);
+    else build_links_kernel<3><<<blocks, 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s)
+{
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
+    if (dim == 2) biofilm_grow_kernel<2><<<blocks, 256, 0, s>>>(g);
+    else biofilm_grow_kernel<3><<<blocks, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s)
+{
+    finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, results);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_to_dense(const ConvArgs &a, cudaStream_t s)
+{
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
+    fields_to_dense_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pop_convert(const PopArgs &a, cudaStream_t s)
+{
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
+    pop_convert_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mfc
+
+using namespace mfc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GraphEntry {
+    int kind, K, fpar, gpar;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct mfc_lattice {
+    mfc_lattice_desc desc;
+    mfc_params prm;
+    int dim = 2, qf = 9, qa = 5, half = 0;
+    int nx = 1, ny = 1, nz = 1, px = 32;
+    long long plane = 0, N = 0;
+    size_t st_bytes = 4;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *f[2] = {nullptr, nullptr};
+    void *g[2] = {nullptr, nullptr};
+    int fcur = 0, gcur = 0;  // buffer holding the current state (read by the next step)
+    void *link = nullptr;
+    int link32 = 0;
+    uint8_t *cls_cur = nullptr, *cls_tmp = nullptr;
+    float *fld_rho = nullptr, *fld_u = nullptr, *fld_c = nullptr;
+    double *partials = nullptr;
+    double *results_d = nullptr, *results_h = nullptr;
+    unsigned long long *counts_d = nullptr, *counts_h = nullptr;
+    double *staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaEvent_t done = nullptr;
+    float c_ref = 1.0f;
+    dim3 grid, block;
+    int rows_per_block = 1, nblocks = 1;
+    std::vector<GraphEntry> graphs;
+    long flow_open = 0, ade_open = 0;
+    double last_current = 0.0;
+    size_t bytes = 0;
+    std::string err;
+    mfc_status sticky = MFC_OK;
+};
+
+namespace {
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+mfc_status fail(mfc_lattice *L, mfc_status s, const std::string &msg)
+{
+    if (L) {
+        L->err = msg;
+        if (s == MFC_ERR_CUDA) L->sticky = s;
+    } else {
+        g_create_error = msg;
+    }
+    return s;
+}
+
+#define CK(L, call)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(L, MFC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+// Make the lattice's device current and refuse work on a lattice with a recorded CUDA error.
+mfc_status enter(mfc_lattice *L)
+{
+    if (!L) return MFC_ERR_ARG;
+    if (L->sticky != MFC_OK) return L->sticky;
+    int cur = -1;
+    CK(L, cudaGetDevice(&cur));
+    if (cur != L->device) CK(L, cudaSetDevice(L->device));
+    return MFC_OK;
+}
+
+mfc_status check_params(const mfc_params *p, std::string *why)
+{
+    auto fin = [](double v) { return isfinite(v) != 0; };
+    if (!p) { *why = "params is NULL"; return MFC_ERR_ARG; }
+    if (!fin(p->tau) || p->tau <= 0.5) { *why = "tau must be > 0.5"; return MFC_ERR_ARG; }
+    if (!fin(p->tau_c) || p->tau_c <= 0.5) { *why = "tau_c must be > 0.5"; return MFC_ERR_ARG; }
+    if (!fin(p->k_sink) || p->k_sink < 0.0 || p->k_sink >= 1.0) {
+        *why = "k_sink must be in [0, 1)";
+        return MFC_ERR_ARG;
+    }
+    if (!fin(p->u_in) || !fin(p->rho_in) || !fin(p->rho_out) || !fin(p->c_in) || !fin(p->c_out) ||
+        !fin(p->u_scale) || p->rho_in <= 0.0 || p->rho_out <= 0.0) {
+        *why = "inlet/outlet parameters must be finite, densities > 0";
+        return MFC_ERR_ARG;
+    }
+    if (p->ade_outlet != MFC_OUTLET_ZERO_GRADIENT && p->ade_outlet != MFC_OUTLET_DIRICHLET) {
+        *why = "ade_outlet must be MFC_OUTLET_ZERO_GRADIENT or MFC_OUTLET_DIRICHLET";
+        return MFC_ERR_ARG;
+    }
+    return MFC_OK;
+}
+
+mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
+{
+    if (!d) { *why = "desc is NULL"; return MFC_ERR_ARG; }
+    if (d->dim != 2 && d->dim != 3) { *why = "dim must be 2 or 3"; return MFC_ERR_ARG; }
+    const int nz = d->dim == 2 ? 1 : d->nz;
+    if (d->nx < 1 || d->ny < 1 || nz < 1) { *why = "sizes must be >= 1"; return MFC_ERR_ARG; }
+    if ((long long)d->nx * d->ny * nz > (1ll << 33)) { *why = "lattice too large"; return MFC_ERR_ARG; }
+    const int fa = d->dim == 2 ? 0 : 2;
+    for (int a = 0; a < d->dim; ++a) {
+        const int b = d->bc[a];
+        if (b != MFC_BC_WALL && b != MFC_BC_PERIODIC && b != MFC_BC_INOUT) {
+            *why = "unknown boundary kind";
+            return MFC_ERR_ARG;
+        }
+        if (b == MFC_BC_INOUT && a != fa) {
+            *why = "MFC_BC_INOUT is only valid on the flow axis (x in 2-D, z in 3-D)";
+            return MFC_ERR_ARG;
+        }
+    }
+    if (d->precision != MFC_FP32 && d->precision != MFC_FP16_DEV) {
+        *why = "precision must be MFC_FP32 or MFC_FP16_DEV";
+        return MFC_ERR_ARG;
+    }
+    return MFC_OK;
+}
+
+struct Layout {
+    int dim, qf, qa, nx, ny, nz, px;
+    long long plane, N;
+    size_t st, link_bytes;
+};
+
+Layout layout_of(const mfc_lattice_desc *d)
+{
+    Layout l;
+    l.dim = d->dim;
+    l.qf = d->dim == 2 ? 9 : 19;
+    l.qa = d->dim == 2 ? 5 : 7;
+    l.nx = d->nx;
+    l.ny = d->ny;
+    l.nz = d->dim == 2 ? 1 : d->nz;
+    l.px = (int)round_up((size_t)l.nx, 32);
+    l.plane = (long long)round_up((size_t)l.px * l.ny * l.nz, 64);
+    l.N = (long long)l.nx * l.ny * l.nz;
+    l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
+    l.link_bytes = d->dim == 2 ? 2 : 4;
+    return l;
+}
+
+// Launch shape: blocks of up to 256 columns; each block walks rows_per_block rows, chosen so the
+// grid holds several waves of the 152 SMs at 8 resident blocks each.
+void choose_launch(mfc_lattice *L)
+{
+    const int bx = L->nx >= 256 ? 256 : (int)round_up((size_t)L->nx, 32);
+    const long long gx = (L->nx + bx - 1) / bx;
+    const long long rows = (long long)L->ny * L->nz;
+    long long r = (gx * rows) / (152ll * 8 * 4);
+    if (r < 1) r = 1;
+    if (r > 16) r = 16;
+    L->block = dim3(bx, 1, 1);
+    L->rows_per_block = (int)r;
+    L->grid = dim3((unsigned)gx, (unsigned)((rows + r - 1) / r), 1);
+    L->nblocks = (int)(L->grid.x * L->grid.y);
+}
+
+void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
+{
+    memset(h, 0, sizeof *h);
+    h->dim = L->dim;
+    h->half = L->half;
+    h->kind = kind;
+    h->mode = mode;
+    h->nx = L->nx; h->ny = L->ny; h->nz = L->nz; h->px = L->px; h->plane = L->plane;
+    h->bc_flow_axis = L->desc.bc[L->dim == 2 ? 0 : 2];
+    h->grid = L->grid;
+    h->block = L->block;
+    h->rows_per_block = L->rows_per_block;
+    h->fsrc = L->f[L->fcur];
+    h->fdst = L->f[1 - L->fcur];
+    h->gsrc = L->g[L->gcur];
+    h->gdst = L->g[1 - L->gcur];
+    h->link = L->link;
+    h->fld_rho = L->fld_rho; h->fld_u = L->fld_u; h->fld_c = L->fld_c;
+    h->partials = L->partials;
+    const mfc_params &p = L->prm;
+    h->omega = (float)(1.0 / p.tau);
+    h->omega_c = (float)(1.0 / p.tau_c);
+    h->k_sink = (float)p.k_sink;
+    h->u_scale = (float)p.u_scale;
+    h->rho_out = (float)p.rho_out;
+    h->c_ref = L->c_ref;
+    h->ade_dirichlet = p.ade_outlet == MFC_OUTLET_DIRICHLET;
+    const int fa = L->dim == 2 ? 0 : 2;
+    for (int i = 0; i < L->qf; ++i) {
+        const int ci = L->dim == 2 ? FlowSet<2>::c(i, fa) : FlowSet<3>::c(i, fa);
+        const double w = L->dim == 2 ? FlowSet<2>::w(i) : FlowSet<3>::w(i);
+        h->bb_in[i] = (float)(2.0 * w * p.rho_in * ci * p.u_in * 3.0);
+    }
+    const double inv_cs2 = L->dim == 2 ? 3.0 : 4.0;
+    for (int i = 0; i < L->qa; ++i) {
+        const int ci = L->dim == 2 ? AdeSet<2>::c(i, fa) : AdeSet<3>::c(i, fa);
+        const double w = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
+        h->gin_dev[i] = (float)(w * p.c_in * (1.0 + ci * p.u_in * inv_cs2) - w * L->c_ref);
+        h->gout_dev[i] = (float)(w * p.c_out * (1.0 + ci * p.u_in * inv_cs2) - w * L->c_ref);
+    }
+}
+
+// Queue one step of `kind` and swap the buffers it wrote.
+mfc_status enqueue_step(mfc_lattice *L, int kind, int mode)
+{
+    StepHost h;
+    fill_step(L, kind, mode, &h);
+    cudaError_t e = L->dim == 2 ? launch_step_2d(h, L->stream) : launch_step_3d(h, L->stream);
+    if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    if (kind != KIND_ADE) L->fcur ^= 1;
+    if (kind != KIND_FLOW) L->gcur ^= 1;
+    return MFC_OK;
+}
+
+// Queue n steps ending with a residual check (n >= 2) or with a field store (n == 1).
+mfc_status enqueue_block(mfc_lattice *L, int kind, int n, bool check)
+{
+    for (int s = 0; s < n; ++s) {
+        int mode = MODE_PLAIN;
+        if (s == n - 1) mode = check ? MODE_CHECK : MODE_WRITE;
+        else if (s == n - 2 && check) mode = MODE_WRITE;
+        mfc_status st = enqueue_step(L, kind, mode);
+        if (st != MFC_OK) return st;
+    }
+    if (check) {
+        CK(L, launch_finalize(L->partials, L->nblocks, L->results_d, L->stream));
+        CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * NRESULT,
+                              cudaMemcpyDeviceToHost, L->stream));
+    }
+    return MFC_OK;
+}
+
+void drop_graphs(mfc_lattice *L)
+{
+    for (auto &g : L->graphs) cudaGraphExecDestroy(g.exec);
+    L->graphs.clear();
+}
+
+// The graph of K (even) steps ending with a check, for the current buffer parity.
+mfc_status graph_for(mfc_lattice *L, int kind, int K, cudaGraphExec_t *out)
+{
+    for (auto &g : L->graphs)
+        if (g.kind == kind && g.K == K && g.fpar == L->fcur && g.gpar == L->gcur) {
+            *out = g.exec;
+            return MFC_OK;
+        }
+    const int f0 = L->fcur, g0 = L->gcur;
+    CK(L, cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    mfc_status st = enqueue_block(L, kind, K, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(L->stream, &graph);
+    L->fcur = f0;  // capture recorded the launches; nothing ran
+    L->gcur = g0;
+    if (st != MFC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    L->graphs.push_back({kind, K, f0, g0, exec});
+    *out = exec;
+    return MFC_OK;
+}
+
+// Wait for the queued work; with a deadline, poll an event and give up at the deadline.
+mfc_status wait_done(mfc_lattice *L, double deadline_s, bool *timed_out)
+{
+    *timed_out = false;
+    CK(L, cudaEventRecord(L->done, L->stream));
+    if (deadline_s <= 0.0) {
+        CK(L, cudaEventSynchronize(L->done));
+        return MFC_OK;
+    }
+    using clk = std::chrono::steady_clock;
+    for (;;) {
+        cudaError_t e = cudaEventQuery(L->done);
+        if (e == cudaSuccess) return MFC_OK;
+        if (e != cudaErrorNotReady) return fail(L, MFC_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e));
+        const double now = std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+        if (now > deadline_s) {
+            *timed_out = true;
+            CK(L, cudaEventSynchronize(L->done));  // the queued work is bounded: let it finish
+            return MFC_OK;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Run one solver (or both, concurrently) to steady state.
+mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, long max_steps, int K,
+                     double deadline, long *steps, double *res_f, double *res_a, bool *converged)
+{
+    *steps = 0;
+    *converged = false;
+    while (*steps < max_steps) {
+        const long left = max_steps - *steps;
+        const int n = left >= K ? K : (int)left;
+        mfc_status st;
+        if (n == K) {
+            cudaGraphExec_t exec;
+            st = graph_for(L, kind, K, &exec);
+            if (st != MFC_OK) return st;
+            CK(L, cudaGraphLaunch(exec, L->stream));
+            if (kind != KIND_ADE && (K & 1)) L->fcur ^= 1;
+            if (kind != KIND_FLOW && (K & 1)) L->gcur ^= 1;
+        } else {
+            st = enqueue_block(L, kind, n, n >= 2);
+            if (st != MFC_OK) return st;
+        }
+        bool to = false;
+        st = wait_done(L, deadline, &to);
+        if (st != MFC_OK) return st;
+        *steps += n;
+        if (n >= 2) {
+            const double *r = L->results_h;
+            if (kind != KIND_ADE) *res_f = r[RES_FLOW];
+            if (kind != KIND_FLOW) {
+                *res_a = r[RES_ADE];
+                L->last_current = r[SUM_CURRENT];
+            }
+            if (r[SUM_BAD] > 0.0 || !isfinite(r[SUM_MASS]) || !isfinite(r[SUM_C]) ||
+                isnan(r[RES_FLOW]) || isnan(r[RES_ADE]))
+                return MFC_ERR_NONFINITE;
+            const bool okf = kind == KIND_ADE || r[RES_FLOW] < tol_flow;
+            const bool oka = kind == KIND_FLOW || r[RES_ADE] < tol_ade;
+            if (okf && oka) {
+                *converged = true;
+                return MFC_OK;
+            }
+        }
+        if (to) return MFC_ERR_TIMEOUT;
+    }
+    return MFC_OK;
+}
+
+void release(mfc_lattice *L)
+{
+    if (!L) return;
+    drop_graphs(L);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(L->f[b]);
+        cudaFree(L->g[b]);
+    }
+    cudaFree(L->link);
+    cudaFree(L->cls_cur);
+    cudaFree(L->cls_tmp);
+    cudaFree(L->fld_rho);
+    cudaFree(L->fld_u);
+    cudaFree(L->fld_c);
+    cudaFree(L->partials);
+    cudaFree(L->results_d);
+    cudaFree(L->counts_d);
+    cudaFree(L->staging);
+    if (L->results_h) cudaFreeHost(L->results_h);
+    if (L->counts_h) cudaFreeHost(L->counts_h);
+    if (L->done) cudaEventDestroy(L->done);
+    if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+}
+
+mfc_status ensure_staging(mfc_lattice *L, size_t bytes)
+{
+    if (L->staging_bytes >= bytes) return MFC_OK;
+    cudaFree(L->staging);
+    L->staging = nullptr;
+    L->staging_bytes = 0;
+    if (cudaMalloc(&L->staging, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(L, MFC_ERR_OOM, "staging allocation failed");
+    }
+    L->staging_bytes = bytes;
+    return MFC_OK;
+}
+
+mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
+{
+    MaskArgs m;
+    memset(&m, 0, sizeof m);
+    m.nx = L->nx; m.ny = L->ny; m.nz = L->nz; m.px = L->px; m.plane = L->plane;
+    for (int a = 0; a < 3; ++a) m.bc[a] = a < L->dim ? L->desc.bc[a] : MFC_BC_PERIODIC;
+    m.cls_new = dev_cls_new;
+    m.cls_old = L->cls_cur;
+    m.reset = reset;
+    m.link = L->link;
+    m.fpop = L->f[L->fcur];
+    m.gpop = L->g[L->gcur];
+    m.half = L->half;
+    m.fld_rho = L->fld_rho; m.fld_u = L->fld_u; m.fld_c = L->fld_c;
+    m.c_ref = L->c_ref;
+    m.counts = L->counts_d;
+    CK(L, cudaMemsetAsync(L->counts_d, 0, 2 * sizeof(unsigned long long), L->stream));
+    CK(L, launch_links(L->dim, m, L->stream));
+    CK(L, cudaMemcpyAsync(L->counts_h, L->counts_d, 2 * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, L->stream));
+    CK(L, cudaStreamSynchronize(L->stream));
+    L->flow_open = (long)L->counts_h[0];
+    L->ade_open = (long)L->counts_h[1];
+    if (dev_cls_new != L->cls_cur) {
+        uint8_t *t = L->cls_cur;
+        L->cls_cur = L->cls_tmp;
+        L->cls_tmp = t;
+    }
+    return MFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
+{
+    std::string why;
+    if (check_desc(desc, &why) != MFC_OK) return 0;
+    Layout l = layout_of(desc);
+    size_t b = 0;
+    b += 2 * (size_t)l.qf * l.plane * l.st;       // flow A/B
+    b += 2 * (size_t)l.qa * l.plane * l.st;       // transport A/B
+    b += (size_t)l.plane * l.link_bytes;          // links
+    b += 2 * round_up((size_t)l.N, 256);          // classes (current, next)
+    b += (size_t)(2 + l.dim) * l.plane * 4;       // fields
+    // partials: at most one block per 256 columns x row
+    b += (size_t)((l.nx + 255) / 256 + 1) * l.ny * l.nz * NSUM * sizeof(double);
+    b += 4096;
+    return b;
+}
+
+MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_params *params,
+                                      mfc_lattice **out)
+{
+    std::string why;
+    if (!out) return fail(nullptr, MFC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    mfc_status st = check_desc(desc, &why);
+    if (st == MFC_OK) st = check_params(params, &why);
+    if (st != MFC_OK) return fail(nullptr, st, why);
+
+    int ndev = 0;
+    cudaError_t de = cudaGetDeviceCount(&ndev);
+    if (de != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, MFC_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(de));
+    }
+    mfc_lattice *L = new (std::nothrow) mfc_lattice();
+    if (!L) return fail(nullptr, MFC_ERR_OOM, "host allocation failed");
+    L->desc = *desc;
+    if (desc->dim == 2) {
+        L->desc.nz = 1;
+        L->desc.bc[2] = MFC_BC_PERIODIC;
+    }
+    L->prm = *params;
+    Layout l = layout_of(desc);
+    L->dim = l.dim; L->qf = l.qf; L->qa = l.qa;
+    L->nx = l.nx; L->ny = l.ny; L->nz = l.nz; L->px = l.px;
+    L->plane = l.plane; L->N = l.N;
+    L->st_bytes = l.st;
+    L->half = desc->precision == MFC_FP16_DEV;
+    L->link32 = desc->dim == 3;
+    L->c_ref = (float)params->c_in;
+    cudaGetDevice(&L->device);
+    choose_launch(L);
+
+    auto dalloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        L->bytes += bytes;
+        return true;
+    };
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && dalloc(&L->f[b], (size_t)l.qf * l.plane * l.st);
+        ok = ok && dalloc(&L->g[b], (size_t)l.qa * l.plane * l.st);
+    }
+    ok = ok && dalloc(&L->link, (size_t)l.plane * l.link_bytes);
+    ok = ok && dalloc((void **)&L->cls_cur, round_up((size_t)l.N, 256));
+    ok = ok && dalloc((void **)&L->cls_tmp, round_up((size_t)l.N, 256));
+    ok = ok && dalloc((void **)&L->fld_rho, (size_t)l.plane * 4);
+    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * l.plane * 4);
+    ok = ok && dalloc((void **)&L->fld_c, (size_t)l.plane * 4);
+    ok = ok && dalloc((void **)&L->partials, (size_t)L->nblocks * NSUM * sizeof(double));
+    ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
+    ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
+    if (!ok) {
+        release(L);
+        delete L;
+        return fail(nullptr, MFC_ERR_OOM, "device allocation failed");
+    }
+    cudaError_t e = cudaHostAlloc((void **)&L->results_h, NRESULT * sizeof(double), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&L->counts_h, 2 * sizeof(unsigned long long), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        if (desc->stream) {
+            L->stream = (cudaStream_t)desc->stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+            L->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        std::string msg = std::string("create: ") + cudaGetErrorString(e);
+        release(L);
+        delete L;
+        return fail(nullptr, MFC_ERR_CUDA, msg);
+    }
+    memset(L->results_h, 0, NRESULT * sizeof(double));
+    // every node open, rest state
+    e = cudaMemsetAsync(L->cls_cur, 0, round_up((size_t)l.N, 256), L->stream);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("create: ") + cudaGetErrorString(e);
+        release(L);
+        delete L;
+        return fail(nullptr, MFC_ERR_CUDA, msg);
+    }
+    st = apply_geometry(L, L->cls_cur, 1);
+    if (st != MFC_OK) {
+        std::string msg = L->err;
+        release(L);
+        delete L;
+        return fail(nullptr, st, msg);
+    }
+    *out = L;
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_destroy_lattice(mfc_lattice *L)
+{
+    if (!L) return MFC_ERR_ARG;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != L->device) cudaSetDevice(L->device);
+    if (L->stream) cudaStreamSynchronize(L->stream);
+    release(L);
+    if (cur >= 0 && cur != L->device) cudaSetDevice(cur);
+    delete L;
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_set_params(mfc_lattice *L, const mfc_params *params)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    std::string why;
+    st = check_params(params, &why);
+    if (st != MFC_OK) return fail(L, st, why);
+    L->prm = *params;
+    drop_graphs(L);  // the graphs hold the old constants
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_set_geometry(mfc_lattice *L, const uint8_t *node_class, int reset_fields)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!node_class) return fail(L, MFC_ERR_ARG, "node_class is NULL");
+    for (long long q = 0; q < L->N; ++q)
+        if (node_class[q] > 7) return fail(L, MFC_ERR_ARG, "node class above 7 at node " + std::to_string(q));
+    CK(L, cudaMemcpyAsync(L->cls_tmp, node_class, (size_t)L->N, cudaMemcpyHostToDevice, L->stream));
+    return apply_geometry(L, L->cls_tmp, reset_fields != 0);
+}
+
+static mfc_status step_n(mfc_lattice *L, int kind, int nsteps)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (nsteps < 0) return fail(L, MFC_ERR_ARG, "nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+        st = enqueue_step(L, kind, s == nsteps - 1 ? MODE_WRITE : MODE_PLAIN);
+        if (st != MFC_OK) return st;
+    }
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_step_flow(mfc_lattice *L, int nsteps) { return step_n(L, KIND_FLOW, nsteps); }
+MFC_API mfc_status mfc_step_ade(mfc_lattice *L, int nsteps) { return step_n(L, KIND_ADE, nsteps); }
+MFC_API mfc_status mfc_step_coupled(mfc_lattice *L, int nsteps) { return step_n(L, KIND_COUPLED, nsteps); }
+
+MFC_API mfc_status mfc_solve_steady(mfc_lattice *L, const mfc_solve_opts *opts, mfc_solve_result *out)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!opts) return fail(L, MFC_ERR_ARG, "opts is NULL");
+    if (opts->max_steps < 0 || opts->check_every < 1 || !(opts->tol_flow >= 0.0) ||
+        !(opts->tol_ade >= 0.0) || (opts->mode != MFC_SEQUENTIAL && opts->mode != MFC_CONCURRENT))
+        return fail(L, MFC_ERR_ARG, "bad solve options");
+    int K = opts->check_every < 2 ? 2 : opts->check_every;
+    if (K & 1) ++K;
+    const double deadline = opts->timeout_s > 0.0 ? now_s() + opts->timeout_s : 0.0;
+    mfc_solve_result r;
+    memset(&r, 0, sizeof r);
+    bool conv_f = false, conv_a = false;
+    if (opts->mode == MFC_SEQUENTIAL) {
+        double dummy = 0.0;
+        st = run_phase(L, KIND_FLOW, opts->tol_flow, 0.0, opts->max_steps, K, deadline, &r.steps_flow,
+                       &r.res_flow, &dummy, &conv_f);
+        r.mass = L->results_h[SUM_MASS];
+        if (st == MFC_OK)
+            st = run_phase(L, KIND_ADE, 0.0, opts->tol_ade, opts->max_steps, K, deadline, &r.steps_ade,
+                           &dummy, &r.res_ade, &conv_a);
+    } else {
+        st = run_phase(L, KIND_COUPLED, opts->tol_flow, opts->tol_ade, opts->max_steps, K, deadline,
+                       &r.steps_flow, &r.res_flow, &r.res_ade, &conv_f);
+        r.steps_ade = r.steps_flow;
+        r.mass = L->results_h[SUM_MASS];
+        conv_a = conv_f;
+    }
+    r.current = L->results_h[SUM_CURRENT];
+    r.substrate = L->results_h[SUM_C];
+    if (st == MFC_OK && !(conv_f && conv_a)) st = MFC_NOT_CONVERGED;
+    r.status = st;
+    if (out) *out = r;
+    return st;
+}
+
+MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *L, uint64_t seed, uint64_t cycle, double prob,
+                                    double c_thresh, long *n_converted)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!(prob >= 0.0 && prob <= 1.0) || !isfinite(c_thresh))
+        return fail(L, MFC_ERR_ARG, "prob must be in [0,1], c_thresh finite");
+    GrowArgs g;
+    memset(&g, 0, sizeof g);
+    g.nx = L->nx; g.ny = L->ny; g.nz = L->nz; g.px = L->px;
+    g.cls = L->cls_cur;
+    g.cls_out = L->cls_tmp;
+    g.fld_c = L->fld_c;
+    g.c_ref = L->c_ref;
+    g.c_thresh = c_thresh;
+    g.seed = seed;
+    g.cycle = cycle;
+    g.lim = (uint64_t)floor(prob * 9007199254740992.0);
+    g.count = L->counts_d;
+    CK(L, cudaMemsetAsync(L->counts_d, 0, sizeof(unsigned long long), L->stream));
+    CK(L, launch_grow(L->dim, g, L->stream));
+    CK(L, cudaMemcpyAsync(L->counts_h, L->counts_d, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          L->stream));
+    CK(L, cudaStreamSynchronize(L->stream));
+    const long n = (long)L->counts_h[0];
+    st = apply_geometry(L, L->cls_tmp, 0);
+    if (st != MFC_OK) return st;
+    if (n_converted) *n_converted = n;
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_read_fields(mfc_lattice *L, double *rho, double *u, double *c, double *current)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    const size_t N = (size_t)L->N;
+    st = ensure_staging(L, (size_t)(2 + L->dim) * N * sizeof(double));
+    if (st != MFC_OK) return st;
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.nx = L->nx; a.ny = L->ny; a.nz = L->nz; a.px = L->px; a.dim = L->dim; a.plane = L->plane;
+    a.link = L->link;
+    a.link32 = L->link32;
+    a.flow_self = 0;
+    a.ade_self = L->qf;
+    a.fld_rho = L->fld_rho; a.fld_u = L->fld_u; a.fld_c = L->fld_c;
+    a.c_ref = L->c_ref;
+    a.rho = rho ? L->staging : nullptr;
+    a.u = u ? L->staging + N : nullptr;
+    a.c = c ? L->staging + (1 + L->dim) * N : nullptr;
+    if (rho || u || c) {
+        CK(L, launch_fields_to_dense(a, L->stream));
+        if (rho) CK(L, cudaMemcpyAsync(rho, a.rho, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        if (u) CK(L, cudaMemcpyAsync(u, a.u, L->dim * N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        if (c) CK(L, cudaMemcpyAsync(c, a.c, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    }
+    CK(L, cudaStreamSynchronize(L->stream));
+    if (current) *current = L->last_current;
+    return MFC_OK;
+}
+
+static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const double *host_in)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!host_out && !host_in) return fail(L, MFC_ERR_ARG, "host buffer is NULL");
+    PopArgs a;
+    memset(&a, 0, sizeof a);
+    a.nx = L->nx; a.ny = L->ny; a.nz = L->nz; a.px = L->px; a.plane = L->plane;
+    a.link = L->link;
+    a.link32 = L->link32;
+    if (which == MFC_POP_FLOW) {
+        a.q = L->qf;
+        a.pop = L->f[L->fcur];
+        a.half = L->half;
+        a.self_bit = 0;
+        a.offset = 1.0f;
+        for (int i = 0; i < a.q; ++i) a.w[i] = L->dim == 2 ? FlowSet<2>::w(i) : FlowSet<3>::w(i);
+    } else if (which == MFC_POP_ADE) {
+        a.q = L->qa;
+        a.pop = L->g[L->gcur];
+        a.half = L->half;
+        a.self_bit = L->qf;
+        a.offset = L->c_ref;
+        for (int i = 0; i < a.q; ++i) a.w[i] = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
+    } else if (which == MFC_FIELD_VELOCITY) {
+        a.q = L->dim;
+        a.pop = L->fld_u;
+        a.half = 0;
+        a.self_bit = host_out ? 0 : -1;
+        a.offset = 0.0f;
+    } else {
+        return fail(L, MFC_ERR_ARG, "unknown population kind");
+    }
+    const size_t bytes = (size_t)a.q * L->N * sizeof(double);
+    st = ensure_staging(L, bytes);
+    if (st != MFC_OK) return st;
+    a.dense = L->staging;
+    a.to_dense = host_out != nullptr;
+    if (host_in) CK(L, cudaMemcpyAsync(L->staging, host_in, bytes, cudaMemcpyHostToDevice, L->stream));
+    CK(L, launch_pop_convert(a, L->stream));
+    if (host_out) CK(L, cudaMemcpyAsync(host_out, L->staging, bytes, cudaMemcpyDeviceToHost, L->stream));
+    CK(L, cudaStreamSynchronize(L->stream));
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_read_populations(mfc_lattice *L, int which, double *host)
+{
+    return pop_io(L, which, host, nullptr);
+}
+
+MFC_API mfc_status mfc_write_populations(mfc_lattice *L, int which, const double *host)
+{
+    return pop_io(L, which, nullptr, host);
+}
+
+MFC_API mfc_status mfc_synchronize(mfc_lattice *L)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    CK(L, cudaStreamSynchronize(L->stream));
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_active_nodes(mfc_lattice *L, long *flow_open, long *ade_open)
+{
+    if (!L) return MFC_ERR_ARG;
+    if (flow_open) *flow_open = L->flow_open;
+    if (ade_open) *ade_open = L->ade_open;
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_device_bytes(mfc_lattice *L, size_t *bytes)
+{
+    if (!L || !bytes) return MFC_ERR_ARG;
+    *bytes = L->bytes + L->staging_bytes;
+    return MFC_OK;
+}
+
+MFC_API const char *mfc_status_string(mfc_status s)
+{
+    switch (s) {
+    case MFC_OK: return "ok";
+    case MFC_ERR_ARG: return "invalid argument";
+    case MFC_ERR_OOM: return "out of device memory";
+    case MFC_ERR_OOM_BUDGET: return "over the memory budget";
+    case MFC_ERR_CUDA: return "CUDA error";
+    case MFC_NOT_CONVERGED: return "not converged within the step cap";
+    case MFC_ERR_NONFINITE: return "non-finite residual, mass or current";
+    case MFC_ERR_TIMEOUT: return "wall-clock limit reached";
+    case MFC_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+MFC_API const char *mfc_last_error(mfc_lattice *L)
+{
+    return L ? L->err.c_str() : g_create_error.c_str();
+}
+
+MFC_API const char *mfc_version(void) { return "mfc 0.1 sm_103a"; }
+
+}  // extern "C"

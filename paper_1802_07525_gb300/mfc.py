@@ -1,0 +1,264 @@
+"""Thin ctypes binding of the C ABI in ``include/mfc.h`` (argument marshalling only).
+
+Every computation runs in the sm_103a library ``_lib/libmfc.so``; this module only converts
+NumPy arrays and Python numbers into the C structures and pointers the library takes.  There
+is no CPU fallback: if the library is missing, :func:`lib` raises.
+
+The raw entry points are available under their C names (``mfc_create_lattice``,
+``mfc_set_geometry``, ``mfc_step_flow``, ``mfc_step_ade``, ``mfc_step_coupled``,
+``mfc_solve_steady``, ``mfc_read_fields``, ...); :class:`Lattice` wraps them for NumPy users.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmfc.so")
+
+MFC_OK, MFC_ERR_ARG, MFC_ERR_OOM, MFC_ERR_OOM_BUDGET, MFC_ERR_CUDA = 0, 1, 2, 3, 4
+MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_TIMEOUT, MFC_ERR_STATE = 5, 6, 7, 8
+MFC_BC_WALL, MFC_BC_PERIODIC, MFC_BC_INOUT = 0, 1, 2
+MFC_FP32, MFC_FP16_DEV = 0, 1
+MFC_SEQUENTIAL, MFC_CONCURRENT = 0, 1
+MFC_OUTLET_ZERO_GRADIENT, MFC_OUTLET_DIRICHLET = 0, 1
+MFC_POP_FLOW, MFC_POP_ADE, MFC_FIELD_VELOCITY = 0, 1, 2
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("tau_c", ctypes.c_double), ("u_in", ctypes.c_double),
+                ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+                ("c_in", ctypes.c_double), ("c_out", ctypes.c_double),
+                ("k_sink", ctypes.c_double), ("u_scale", ctypes.c_double),
+                ("ade_outlet", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol_flow", ctypes.c_double), ("tol_ade", ctypes.c_double),
+                ("max_steps", ctypes.c_long), ("check_every", ctypes.c_int),
+                ("mode", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("steps_flow", ctypes.c_long), ("steps_ade", ctypes.c_long),
+                ("res_flow", ctypes.c_double), ("res_ade", ctypes.c_double),
+                ("current", ctypes.c_double), ("mass", ctypes.c_double),
+                ("substrate", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MfcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "mfc_create_lattice": (ctypes.c_int, [ctypes.POINTER(LatticeDesc), ctypes.POINTER(Params),
+                                          ctypes.POINTER(_vp)]),
+    "mfc_destroy_lattice": (ctypes.c_int, [_vp]),
+    "mfc_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(Params)]),
+    "mfc_set_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int]),
+    "mfc_step_flow": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mfc_step_ade": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mfc_step_coupled": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mfc_solve_steady": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveResult)]),
+    "mfc_biofilm_grow": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_long)]),
+    "mfc_read_fields": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "mfc_read_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "mfc_write_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "mfc_synchronize": (ctypes.c_int, [_vp]),
+    "mfc_active_nodes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_long),
+                                        ctypes.POINTER(ctypes.c_long)]),
+    "mfc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "mfc_lattice_bytes": (ctypes.c_size_t, [ctypes.POINTER(LatticeDesc)]),
+    "mfc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mfc_last_error": (ctypes.c_char_p, [_vp]),
+    "mfc_version": (ctypes.c_char_p, []),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libmfc.so (built by ``paper_1802_07525_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(
+                        f"CUDA library not built: {LIB_PATH} is missing; run "
+                        "`python -m paper_1802_07525_gb300.build` (needs nvcc)")
+                L = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in _SIGS.items():
+                    fn = getattr(L, name)
+                    fn.restype = res
+                    fn.argtypes = args
+                _lib = L
+    return _lib
+
+
+def __getattr__(name):
+    if name in _SIGS:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def status_string(s: int) -> str:
+    return lib().mfc_status_string(s).decode()
+
+
+def _ptr(a, ct=ctypes.c_double):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def make_params(tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0, c_out=0.0,
+                k_sink=1e-3, u_scale=1.0, ade_outlet=MFC_OUTLET_ZERO_GRADIENT) -> Params:
+    return Params(tau, tau_c, u_in, rho_in, rho_out, c_in, c_out, k_sink, u_scale, ade_outlet)
+
+
+def make_desc(shape, bc=None, precision=MFC_FP32, stream=None) -> LatticeDesc:
+    shape = tuple(int(s) for s in shape)
+    dim = len(shape)
+    if bc is None:
+        bc = (MFC_BC_INOUT, MFC_BC_WALL) if dim == 2 else (MFC_BC_WALL, MFC_BC_WALL, MFC_BC_INOUT)
+    bcs = list(bc) + [MFC_BC_PERIODIC] * (3 - len(bc))
+    d = LatticeDesc()
+    d.dim = dim
+    d.nx, d.ny = shape[0], shape[1]
+    d.nz = shape[2] if dim == 3 else 1
+    for a in range(3):
+        d.bc[a] = bcs[a]
+    d.precision = precision
+    d.stream = stream
+    return d
+
+
+def lattice_bytes(shape, bc=None, precision=MFC_FP32) -> int:
+    return int(lib().mfc_lattice_bytes(ctypes.byref(make_desc(shape, bc, precision))))
+
+
+class Lattice:
+    """One lattice resident on the current CUDA device (see ``include/mfc.h``)."""
+
+    def __init__(self, shape, *, bc=None, precision=MFC_FP32, stream=None, **params):
+        self.shape = tuple(int(s) for s in shape)
+        self.dim = len(self.shape)
+        self.N = int(np.prod(self.shape))
+        self.qf = 9 if self.dim == 2 else 19
+        self.qa = 5 if self.dim == 2 else 7
+        self._L = lib()
+        self.desc = make_desc(self.shape, bc, precision, stream)
+        self.params = make_params(**params)
+        h = ctypes.c_void_p()
+        st = self._L.mfc_create_lattice(ctypes.byref(self.desc), ctypes.byref(self.params),
+                                        ctypes.byref(h))
+        if st != MFC_OK:
+            raise MfcError(st, self._L.mfc_last_error(None).decode())
+        self.handle = h
+
+    def _check(self, st, ok=(MFC_OK,)):
+        if st not in ok:
+            raise MfcError(st, self._L.mfc_last_error(self.handle).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.mfc_destroy_lattice(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, **params):
+        self.params = make_params(**params)
+        self._check(self._L.mfc_set_params(self.handle, ctypes.byref(self.params)))
+
+    def set_geometry(self, node_class, reset_fields=True):
+        c = np.ascontiguousarray(np.asarray(node_class, dtype=np.uint8).reshape(-1))
+        if c.size != self.N:
+            raise ValueError(f"node_class has {c.size} entries, lattice has {self.N}")
+        self._check(self._L.mfc_set_geometry(self.handle, _ptr(c, ctypes.c_uint8),
+                                             int(bool(reset_fields))))
+
+    def step_flow(self, n=1):
+        self._check(self._L.mfc_step_flow(self.handle, int(n)))
+
+    def step_ade(self, n=1):
+        self._check(self._L.mfc_step_ade(self.handle, int(n)))
+
+    def step_coupled(self, n=1):
+        self._check(self._L.mfc_step_coupled(self.handle, int(n)))
+
+    def solve_steady(self, mode=MFC_SEQUENTIAL, tol_flow=1e-8, tol_ade=1e-8, max_steps=10000,
+                     check_every=100, timeout_s=0.0) -> SolveResult:
+        o = SolveOpts(tol_flow, tol_ade, int(max_steps), int(check_every), mode, timeout_s)
+        r = SolveResult()
+        # the result is filled for these outcomes; its status field says which one it was
+        self._check(self._L.mfc_solve_steady(self.handle, ctypes.byref(o), ctypes.byref(r)),
+                    ok=(MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_TIMEOUT, MFC_ERR_NONFINITE))
+        return r
+
+    def biofilm_grow(self, seed, cycle, prob=0.05, c_thresh=0.5) -> int:
+        n = ctypes.c_long(0)
+        self._check(self._L.mfc_biofilm_grow(self.handle, seed, cycle, prob, c_thresh,
+                                             ctypes.byref(n)))
+        return int(n.value)
+
+    def read_fields(self):
+        rho = np.empty(self.N)
+        u = np.empty((self.dim, self.N))
+        c = np.empty(self.N)
+        cur = np.zeros(1)
+        self._check(self._L.mfc_read_fields(self.handle, _ptr(rho), _ptr(u), _ptr(c), _ptr(cur)))
+        return rho, u, c, float(cur[0])
+
+    def read_populations(self, which=MFC_POP_FLOW):
+        q = {MFC_POP_FLOW: self.qf, MFC_POP_ADE: self.qa, MFC_FIELD_VELOCITY: self.dim}[which]
+        out = np.empty((q, self.N))
+        self._check(self._L.mfc_read_populations(self.handle, which, _ptr(out)))
+        return out
+
+    def write_populations(self, which, values):
+        q = {MFC_POP_FLOW: self.qf, MFC_POP_ADE: self.qa, MFC_FIELD_VELOCITY: self.dim}[which]
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(q, self.N))
+        self._check(self._L.mfc_write_populations(self.handle, which, _ptr(v)))
+
+    def synchronize(self):
+        self._check(self._L.mfc_synchronize(self.handle))
+
+    def active_nodes(self):
+        a, b = ctypes.c_long(), ctypes.c_long()
+        self._check(self._L.mfc_active_nodes(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
+    def device_bytes(self):
+        b = ctypes.c_size_t()
+        self._check(self._L.mfc_device_bytes(self.handle, ctypes.byref(b)))
+        return int(b.value)

@@ -1,0 +1,317 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on seeded synthetic inputs.
+
+Tolerances (FP32 storage and arithmetic against the FP64 oracle):
+  - populations over the first 1000 steps: max-abs 1e-5;
+  - steady velocity and concentration fields: relative L2 1e-4; integrated current: relative 1e-4;
+  - integer work (link masks via node classes, biofilm growth): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import mfc_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+FIELD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1802_07525_gb300 import build
+    build.build()
+    import paper_1802_07525_gb300 as P
+    return P
+
+
+def pair(P, shape, cls, bc=None, precision=0, **kw):
+    """A GPU lattice and an oracle lattice with the same geometry and parameters."""
+    dim = len(shape)
+    if bc is None:
+        bc = (2, 0) if dim == 2 else (0, 0, 2)
+    g = P.Lattice(shape, bc=bc, precision=precision, **kw)
+    g.set_geometry(cls, reset_fields=True)
+    o = oracle.Oracle(shape, cls, bc=bc, **kw)
+    return g, o
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def channel_kw(w):
+    return dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
+
+
+# ------------------------------------------------------------------------------------------
+# Per-step populations
+# ------------------------------------------------------------------------------------------
+
+def test_channel_128x64_coupled_populations_first_1000_steps(P):
+    """Fused flow + transport on the 128x64 channel: populations within 1e-5 of the oracle
+    at steps 1, 10, 100, 1000."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **channel_kw(w))
+    done = 0
+    for target in (1, 10, 100, 1000):
+        g.step_coupled(target - done)
+        o.step_coupled(target - done)
+        done = target
+        assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL, target
+        assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL, target
+    rho, u, c, _ = g.read_fields()
+    assert maxabs(rho, o.rho) < POP_TOL
+    assert maxabs(u, o.u) < POP_TOL
+    assert maxabs(c, o.conc) < POP_TOL
+
+
+def test_channel_128x64_sequential_populations(P):
+    """Flow steps, then transport steps with that velocity frozen (the paper's order)."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **channel_kw(w))
+    g.step_flow(300)
+    o.step_flow(300)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_FIELD_VELOCITY), o.u) < POP_TOL
+    g.step_ade(300)
+    o.step_ade(300)
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+    assert maxabs(g.read_fields()[2], o.conc) < POP_TOL
+
+
+@pytest.mark.parametrize("shape,bc", [
+    ((37, 23), (2, 0)),          # ragged: not a multiple of the warp or block width
+    ((300, 9), (2, 1)),          # periodic cross axis, two column blocks with a ragged tail
+    ((20, 16), (1, 1)),          # fully periodic
+    ((17, 11), (0, 0)),          # closed box
+    ((1, 5), (0, 0)),            # one column
+    ((3, 1), (2, 1)),            # one row, periodic
+])
+def test_2d_boundary_kinds_and_ragged_sizes(P, shape, bc):
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N)
+    r = rng.random(N)
+    cls = np.where(r < 0.15, 3, np.where(r < 0.3, 4, np.where(r < 0.35, 5, 0))).astype(np.uint8)
+    g, o = pair(P, shape, cls, bc=bc, tau=0.7, tau_c=0.9, u_in=0.03, c_in=0.8, k_sink=0.01)
+    if bc[0] != 2:
+        # no inlet: start from a perturbed state so something moves
+        f = o.f.copy()
+        open_ = (cls & 1) == 0
+        for k in np.nonzero(open_)[0]:
+            f[:, k] = oracle.flow_equilibrium(2, 1.0 + 0.01 * rng.standard_normal(),
+                                              0.02 * rng.standard_normal(2))
+        gg = np.where((cls & 2) == 0, rng.random((5, N)) * 0.2, 0.0)
+        o.f[:] = f
+        o.g[:] = gg
+        g.write_populations(P.MFC_POP_FLOW, f)
+        g.write_populations(P.MFC_POP_ADE, gg)
+    g.step_coupled(200)
+    o.step_coupled(200)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+
+
+def test_dirichlet_outlet_and_velocity_scale(P):
+    shape = (40, 12)
+    cls = mi.mark_sink_layer(shape, mi.bernoulli_block(shape, 0.2, 5, block=(10, 30)), mi.SINK)
+    kw = dict(tau=0.8, tau_c=0.75, u_in=0.02, c_in=1.0, c_out=0.25, k_sink=5e-3, u_scale=2.5,
+              ade_outlet=1)
+    g, o = pair(P, shape, cls, **kw)
+    g.step_flow(150)
+    o.step_flow(150)
+    g.step_ade(150)
+    o.step_ade(150)
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+
+
+@pytest.mark.parametrize("shape,bc", [((24, 20, 32), (0, 0, 2)), ((19, 13, 11), (1, 0, 2)),
+                                      ((12, 10, 9), (1, 1, 1))])
+def test_3d_populations(P, shape, bc):
+    cls = mi.overlapping_balls(shape, 3, 0.7, 31)
+    cls = mi.mark_sink_layer(shape, cls, mi.SINK)
+    kw = dict(tau=0.7, tau_c=0.6, u_in=0.005, c_in=1.0, k_sink=5e-4)
+    g, o = pair(P, shape, cls, bc=bc, **kw)
+    if bc[2] != 2:
+        rng = np.random.default_rng(3)
+        gg = np.where((cls & 2) == 0, rng.random((7, g.N)) * 0.1, 0.0)
+        o.g[:] = gg
+        g.write_populations(P.MFC_POP_ADE, gg)
+    g.step_coupled(100)
+    o.step_coupled(100)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+
+
+# ------------------------------------------------------------------------------------------
+# Steady state, residuals, current
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_channel_128x64_steady_fields_and_current(P, mode):
+    """Solve to tol 1e-8 or 10^4 steps with a residual check every 100 steps, on both sides;
+    fields within 1e-4 relative L2, current within 1e-4 relative."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **channel_kw(w))
+    rg = g.solve_steady(mode=mode, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    ro = o.solve_steady(mode=mode, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    rho, u, c, cur = g.read_fields()
+    assert rel_l2(u, o.u) < FIELD_TOL
+    assert rel_l2(c, o.conc) < FIELD_TOL
+    assert abs(rg.current - ro.current) / ro.current < FIELD_TOL
+    assert abs(cur - ro.current) / ro.current < FIELD_TOL
+    assert abs(rg.mass - ro.mass) / ro.mass < 1e-6
+    # same stopping decisions, or both at the cap
+    assert rg.steps_flow == ro.steps_flow or max(rg.res_flow, ro.res_flow) < 3 * w.tol
+    assert rg.status in (P.MFC_OK, P.MFC_NOT_CONVERGED)
+
+
+def test_residual_sums_match_oracle_sums(P):
+    """The FP64 reductions of a check step agree with the oracle's sums of the same fields:
+    400 fused steps, then a 2-step solve block (store fields at 401, compare at 402)."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **channel_kw(w))
+    g.step_coupled(400)
+    r = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=2, check_every=2)
+    o.step_coupled(401)
+    u1, c1 = o.u.copy(), o.conc.copy()
+    o.step_coupled(1)
+    s = o.sums(u1, c1)
+    assert r.status == P.MFC_NOT_CONVERGED and r.steps_flow == 2
+    assert r.res_flow == pytest.approx(np.sqrt(s[0] / s[1]), rel=1e-3)
+    assert r.res_ade == pytest.approx(np.sqrt(s[3] / s[4]), rel=1e-3)
+    assert r.current == pytest.approx(s[6], rel=1e-5)
+    assert r.mass == pytest.approx(s[2], rel=1e-7)
+    assert r.substrate == pytest.approx(s[5], rel=1e-5)
+
+
+def test_solve_statuses_and_host_injected_nonfinite(P):
+    w = mi.channel_128x64()
+    g = P.Lattice(w.shape, **channel_kw(w))
+    g.set_geometry(w.cls)
+    r = g.solve_steady(mode=1, tol_flow=1e-30, tol_ade=1e-30, max_steps=10, check_every=4)
+    assert r.status == P.MFC_NOT_CONVERGED and r.steps_flow == 10
+    r = g.solve_steady(mode=1, tol_flow=1e-30, tol_ade=1e-30, max_steps=10**7, check_every=100,
+                       timeout_s=0.05)
+    assert r.status == P.MFC_ERR_TIMEOUT
+    # inject a NaN into the populations on the host; the residual check reports it
+    f = g.read_populations(P.MFC_POP_FLOW)
+    k = int(np.nonzero((w.cls & 1) == 0)[0][100])
+    f[3, k] = np.nan
+    g.write_populations(P.MFC_POP_FLOW, f)
+    r = g.solve_steady(mode=1, tol_flow=1e-8, tol_ade=1e-8, max_steps=100, check_every=10)
+    assert r.status == P.MFC_ERR_NONFINITE and r.steps_flow == 10
+    # the lattice stays usable after a reset
+    g.set_geometry(w.cls, reset_fields=True)
+    g.step_coupled(5)
+    assert np.isfinite(g.read_fields()[1]).all()
+
+
+# ------------------------------------------------------------------------------------------
+# Geometry updates and the biofilm rule
+# ------------------------------------------------------------------------------------------
+
+def test_biofilm_growth_bit_exact_and_warm_start(P):
+    """The GPU growth pass equals the oracle's rule applied to the GPU's own concentration
+    field (the threshold is decided in the same precision); the warm-started step after the
+    mask change matches the oracle stepping from the same state."""
+    shape = (96, 48)
+    cls = mi.mark_sink_layer(shape, mi.overlapping_balls(shape, 4, 0.75, 12), mi.SINK)
+    kw = dict(tau=0.8, tau_c=0.7, u_in=0.02, c_in=1.0, k_sink=1e-3)
+    g, o = pair(P, shape, cls, **kw)
+    g.step_coupled(800)
+    c_gpu = g.read_fields()[2]
+    f_gpu = g.read_populations(P.MFC_POP_FLOW)
+    g_gpu = g.read_populations(P.MFC_POP_ADE)
+    for cycle in range(3):
+        new_o, n_o = o.biofilm_convert(77, cycle, prob=0.3, c_thresh=0.5, conc=c_gpu)
+        n_g = g.biofilm_grow(77, cycle, prob=0.3, c_thresh=0.5)
+        assert n_g == n_o and n_o > 0
+        o.cls[:] = new_o
+        # the GPU's flow-blocked set (populations read as 0 there) equals the oracle's mask
+        fb = np.all(g.read_populations(P.MFC_POP_FLOW) == 0.0, axis=0)
+        assert np.array_equal(fb, (o.cls & 1) > 0)
+        c_gpu = g.read_fields()[2]
+    # warm start: oracle steps from the GPU's populations with the grown mask
+    o2 = oracle.Oracle(shape, o.cls, **kw)
+    newly_solid = (o.cls & 1) & ~(cls & 1)
+    f0 = f_gpu.copy()
+    f0[:, newly_solid > 0] = 0.0
+    o2.f[:] = f0
+    o2.g[:] = g_gpu
+    # the GPU kept the same populations (no steps since the read)
+    o2.step_coupled(20)
+    g.step_coupled(20)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o2.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o2.g) < POP_TOL
+
+
+def test_set_geometry_warm_start_opens_and_closes_nodes(P):
+    shape = (40, 20)
+    rng = np.random.default_rng(1)
+    cls1 = np.where(rng.random(800) < 0.2, 3, 0).astype(np.uint8)
+    cls2 = np.where(rng.random(800) < 0.2, 3, 0).astype(np.uint8)
+    g, o = pair(P, shape, cls1, tau=0.9, tau_c=0.8, u_in=0.02)
+    g.step_coupled(50)
+    o.step_coupled(50)
+    g.set_geometry(cls2, reset_fields=False)
+    # oracle: keep populations where open in both, rest state where newly open, drop newly blocked
+    f = o.f.copy()
+    gg = o.g.copy()
+    opened_f = ((cls1 & 1) > 0) & ((cls2 & 1) == 0)
+    opened_a = ((cls1 & 2) > 0) & ((cls2 & 2) == 0)
+    wf = oracle.flow_equilibrium(2, 1.0, [0, 0])
+    f[:, opened_f] = wf[:, None]
+    gg[:, opened_a] = 0.0
+    f[:, (cls2 & 1) > 0] = 0.0
+    gg[:, (cls2 & 2) > 0] = 0.0
+    o2 = oracle.Oracle(shape, cls2, tau=0.9, tau_c=0.8, u_in=0.02)
+    o2.f[:] = f
+    o2.g[:] = gg
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o2.f) < POP_TOL
+    g.step_coupled(30)
+    o2.step_coupled(30)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o2.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o2.g) < POP_TOL
+    assert g.active_nodes() == (int(((cls2 & 1) == 0).sum()), int(((cls2 & 2) == 0).sum()))
+
+
+# ------------------------------------------------------------------------------------------
+# Full size, in the launch configuration the benchmark times
+# ------------------------------------------------------------------------------------------
+
+def test_anode_2048x1024_one_step_parity_at_full_size(P):
+    """2048x1024 porous anode after 300 fused steps: one more GPU step equals one oracle step
+    taken from the GPU's own state (every node), and the check-step sums equal the oracle's."""
+    w = mi.anode_2d()
+    g = P.Lattice(w.shape, **channel_kw(w))
+    g.set_geometry(w.cls)
+    g.step_coupled(300)
+    f = g.read_populations(P.MFC_POP_FLOW)
+    gg = g.read_populations(P.MFC_POP_ADE)
+    o = oracle.Oracle(w.shape, w.cls, **channel_kw(w))
+    o.f[:] = f
+    o.g[:] = gg
+    o.step_coupled(1)
+    g.step_coupled(1)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < 1e-6
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < 1e-6
+    rho, u, c, _ = g.read_fields()
+    assert maxabs(u, o.u) < 1e-6 and maxabs(c, o.conc) < 1e-6
+
+
+def test_fp16_deviation_storage_error_is_bounded(P):
+    """FP16 deviation storage: error against the FP64 oracle stays small (stated, not 1e-5)."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, precision=1, **channel_kw(w))
+    g.step_coupled(1000)
+    o.step_coupled(1000)
+    rho, u, c, _ = g.read_fields()
+    assert rel_l2(u, o.u) < 2e-2
+    assert rel_l2(c, o.conc) < 2e-3
