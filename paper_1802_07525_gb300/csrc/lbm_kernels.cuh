@@ -11,8 +11,10 @@
 // ghost at c_in and a zero-gradient (or Dirichlet) outlet, BGK relaxation to the linear
 // equilibrium w_i C (1 + c_i.u / cs^2), and the consumption w_i k C on sink nodes.
 //
-// Populations are stored as deviations from rest (f_i - w_i, g_i - w_i c_ref) so that FP32
-// (or FP16) keeps the small velocity-carrying part; arithmetic is FP32.  Check steps accumulate
+// Flow populations are stored as deviations from rest (f_i - w_i) so that FP32 (or FP16) keeps
+// the small velocity-carrying part; transport populations as g_i - w_i c_ref (c_ref = 0 in FP32,
+// where the no-substrate start state is then exact).  Arithmetic is FP32.  The rest population
+// of each lattice is written as the conserved total minus the moving ones.  Check steps accumulate
 // the residual, mass, substrate and current sums in FP64 (warp shuffles, then shared memory,
 // one partial per block; a single-block kernel adds the partials in a fixed order).
 #pragma once
@@ -201,14 +203,20 @@ __device__ __forceinline__ void update_node(const StepArgs<DIM, ST> &a, int x, i
             u[ax] = j[ax] * inv;
             uu += u[ax] * u[ax];
         }
+        // BGK relaxation of the moving populations; the rest population takes what closes the
+        // mass exactly (collision conserves sum_i f_i), so FP32 rounding cannot drift the mass.
+        float moved = 0.f;
 #pragma unroll
-        for (int i = 0; i < F::Q; ++i) {
+        for (int i = 1; i < F::Q; ++i) {
             float cu = 0.f;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cu += F::c(i, ax) * u[ax];
             const float feq = F::w(i) * (rp + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-            st(a.fdst + (long long)i * a.plane + k, d[i] + a.omega * (feq - d[i]));
+            const float v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
+            st(a.fdst + (long long)i * a.plane + k, v);
+            moved += v;
         }
+        st(a.fdst + k, rp - moved);
         if (MODE != MODE_PLAIN) {
             if (MODE == MODE_CHECK) {
                 double du2 = 0.0, u2 = 0.0;
@@ -265,14 +273,19 @@ __device__ __forceinline__ void update_node(const StepArgs<DIM, ST> &a, int x, i
         for (int i = 0; i < A::Q; ++i) cp += e[i];
         const float C = a.c_ref + cp;
         const float sink = (L & (1u << LK::SINK)) ? a.k_sink * C : 0.0f;
+        // Same closure: after relaxation and consumption the populations hold C - kC exactly.
+        float moved = 0.f;
 #pragma unroll
-        for (int i = 0; i < A::Q; ++i) {
+        for (int i = 1; i < A::Q; ++i) {
             float cu = 0.f;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cu += A::c(i, ax) * u[ax];
             const float geq = A::w(i) * (cp + C * cu * A::inv_cs2);
-            st(a.gdst + (long long)i * a.plane + k, e[i] + a.omega_c * (geq - e[i]) - A::w(i) * sink);
+            const float v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - A::w(i) * sink);
+            st(a.gdst + (long long)i * a.plane + k, v);
+            moved += v;
         }
+        st(a.gdst + k, cp - sink - moved);
         if (MODE != MODE_PLAIN) {
             if (MODE == MODE_CHECK) {
                 const double Cn = (double)a.c_ref + (double)cp;

@@ -97,6 +97,9 @@ __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+// The value a store of v keeps (identity in FP32, rounded to FP16 in FP16 storage).
+__device__ __forceinline__ float kept(const float *, float v) { return v; }
+__device__ __forceinline__ float kept(const __half *, float v) { return __half2float(__float2half_rn(v)); }
 
 // Sums produced by a residual-check step (one double each, per block then per lattice).
 enum : int {
