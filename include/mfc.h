@@ -31,8 +31,8 @@
  *   - Errors: every call returns an mfc_status; nothing aborts or exits.  A CUDA error is
  *     recorded on the lattice and returned by that call and every later call on it.
  *   - Precision: flow populations are stored as deviations from rest (f_i - w_i), transport
- *     populations as g_i - w_i*c_ref (c_ref = 0 in FP32, c_in/2 in FP16), in FP32 (MFC_FP32)
- *     or FP16 (MFC_FP16_DEV); arithmetic is FP32; residual, mass and current sums are FP64.
+ *     populations as they are (g_i), in FP32 (MFC_FP32) or FP16 (MFC_FP16_DEV); arithmetic is
+ *     FP32; residual, mass and current sums are FP64.
  */
 #ifndef MFC_H
 #define MFC_H

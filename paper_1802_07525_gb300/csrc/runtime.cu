@@ -535,9 +535,8 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     L->st_bytes = l.st;
     L->half = desc->precision == MFC_FP16_DEV;
     L->link32 = desc->dim == 3;
-    // transport storage offset: 0 in FP32 (the no-substrate start state is exact); half the
-    // inlet concentration in FP16, which halves the largest stored magnitude
-    L->c_ref = desc->precision == MFC_FP16_DEV ? (float)(0.5 * params->c_in) : 0.0f;
+    // transport storage offset: 0, so that the no-substrate start state is stored exactly
+    L->c_ref = 0.0f;
     cudaGetDevice(&L->device);
     choose_launch(L);
 
