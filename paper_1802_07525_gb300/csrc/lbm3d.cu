@@ -1,25 +1,31 @@
-// 3-D instantiations of the fused stream-collide kernel (flow D3Q19, transport D3Q7).
+// 3-D instantiations of the fused stream-collide kernel (flow D3Q19, transport D3Q7),
+// 2 nodes per thread, and of the ghost fill.
 #include "mfc_internal.h"
 
 namespace mfc {
 
+namespace {
+
+constexpr int VW = 2;
+
 template <typename ST, bool FLOW, bool ADE>
-static cudaError_t launch_mode(const StepArgs<3, ST> &a, const StepHost &h, cudaStream_t s)
+cudaError_t launch_mode(const StepArgs<3, ST> &a, const StepHost &h, cudaStream_t s)
 {
     switch (h.mode) {
-    case MODE_PLAIN: lbm_step_kernel<3, ST, FLOW, ADE, MODE_PLAIN><<<h.grid, h.block, 0, s>>>(a); break;
-    case MODE_WRITE: lbm_step_kernel<3, ST, FLOW, ADE, MODE_WRITE><<<h.grid, h.block, 0, s>>>(a); break;
-    default: lbm_step_kernel<3, ST, FLOW, ADE, MODE_CHECK><<<h.grid, h.block, 0, s>>>(a); break;
+    case MODE_PLAIN: lbm_step_kernel<3, ST, FLOW, ADE, MODE_PLAIN, VW><<<h.grid, h.block, 0, s>>>(a); break;
+    case MODE_WRITE: lbm_step_kernel<3, ST, FLOW, ADE, MODE_WRITE, VW><<<h.grid, h.block, 0, s>>>(a); break;
+    default: lbm_step_kernel<3, ST, FLOW, ADE, MODE_CHECK, VW><<<h.grid, h.block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
-template <typename ST> static cudaError_t launch_typed(const StepHost &h, cudaStream_t s)
+template <typename ST> StepArgs<3, ST> make_args(const StepHost &h)
 {
     StepArgs<3, ST> a;
-    a.nx = h.nx; a.ny = h.ny; a.nz = h.nz; a.px = h.px; a.plane = h.plane;
-    a.bc_flow_axis = h.bc_flow_axis;
-    a.rows_per_block = h.rows_per_block;
+    a.geo = h.geo;
+    for (int i = 0; i < 3; ++i) a.bc[i] = h.bc[i];
+    a.gpr = h.gpr;
+    a.ngroups = h.ngroups;
     a.fsrc = static_cast<const ST *>(h.fsrc);
     a.fdst = static_cast<ST *>(h.fdst);
     a.gsrc = static_cast<const ST *>(h.gsrc);
@@ -34,6 +40,12 @@ template <typename ST> static cudaError_t launch_typed(const StepHost &h, cudaSt
         a.gin_dev[i] = h.gin_dev[i];
         a.gout_dev[i] = h.gout_dev[i];
     }
+    return a;
+}
+
+template <typename ST> cudaError_t launch_typed(const StepHost &h, cudaStream_t s)
+{
+    const StepArgs<3, ST> a = make_args<ST>(h);
     switch (h.kind) {
     case KIND_COUPLED: return launch_mode<ST, true, true>(a, h, s);
     case KIND_FLOW: return launch_mode<ST, true, false>(a, h, s);
@@ -41,9 +53,25 @@ template <typename ST> static cudaError_t launch_typed(const StepHost &h, cudaSt
     }
 }
 
+template <typename ST> cudaError_t fill_typed(const StepHost &h, cudaStream_t s)
+{
+    const StepArgs<3, ST> a = make_args<ST>(h);
+    const long long N = (long long)h.geo.nx * h.geo.ny * h.geo.nz;
+    const long long b = (N + 255) / 256;
+    fill_ghosts_kernel<3, ST><<<(int)(b < 65535 ? b : 65535), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_step_3d(const StepHost &h, cudaStream_t s)
 {
     return h.half ? launch_typed<__half>(h, s) : launch_typed<float>(h, s);
+}
+
+cudaError_t launch_fill_ghosts_3d(const StepHost &h, cudaStream_t s)
+{
+    return h.half ? fill_typed<__half>(h, s) : fill_typed<float>(h, s);
 }
 
 }  // namespace mfc

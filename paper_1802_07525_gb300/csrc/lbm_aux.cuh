@@ -1,5 +1,6 @@
 // Reduction finalize, link-mask construction, dense conversion and biofilm growth kernels
-// (included by the runtime only).
+// (included by the runtime only).  All of them walk the lattice nodes in dense order
+// (x fastest) and address the pitched ghost layout through Geo::at.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -42,18 +43,22 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double *partials, i
     }
 }
 
-// ---- geometry ------------------------------------------------------------------------------
+__device__ __forceinline__ void node_xyz(const Geo &g, long long q, int *x, int *y, int *z)
+{
+    *x = (int)(q % g.nx);
+    *y = (int)((q / g.nx) % g.ny);
+    *z = (int)(q / ((long long)g.nx * g.ny));
+}
 
-
-
-// Is the link that brings a population along (cx,cy,cz) to (x,y,z) blocked?  Walls win over the
-// inlet and outlet; an outlet source is moved back onto the last layer, whose class decides.
+// Is the link that brings a population along (cx,cy,cz) to (x,y,z) blocked (Eq. 11)?  Walls win
+// over the inlet and outlet; a periodic source wraps; an outlet source moves back onto the last
+// layer, whose class decides.
 template <int DIM>
 __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, int z, int cx, int cy,
                                              int cz, uint8_t bit)
 {
     int s[3] = {x - cx, y - cy, z - cz};
-    const int n[3] = {m.nx, m.ny, m.nz};
+    const int n[3] = {m.geo.nx, m.geo.ny, m.geo.nz};
     constexpr int FA = DIM == 2 ? 0 : 2;
     for (int ax = 0; ax < DIM; ++ax) {
         const bool out = s[ax] < 0 || s[ax] >= n[ax];
@@ -68,55 +73,53 @@ __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, in
             s[ax] = n[ax] - 1;            // outlet: the last layer decides
         }
     }
-    return (m.cls_new[s[0] + (long long)m.nx * (s[1] + (long long)m.ny * s[2])] & bit) != 0;
+    return (m.cls_new[s[0] + (long long)m.geo.nx * (s[1] + (long long)m.geo.ny * s[2])] & bit) != 0;
 }
 
+// Link words from the node classes; (re)initialise populations and fields of nodes whose class
+// changed (or of every node when resetting); count the open nodes.
 template <int DIM> __global__ void build_links_kernel(const MaskArgs m)
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM>;
     using LK = Links<DIM>;
     using LinkT = typename LK::T;
-    const long long N = (long long)m.nx * m.ny * m.nz;
+    const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(q % m.nx);
-        const int y = (int)((q / m.nx) % m.ny);
-        const int z = (int)(q / ((long long)m.nx * m.ny));
-        const long long k = x + (long long)m.px * (y + (long long)m.ny * z);
+        int x, y, z;
+        node_xyz(m.geo, q, &x, &y, &z);
+        const long long k = m.geo.at(x, y, z);
         const uint8_t c = m.cls_new[q];
         uint32_t L = 0;
         if (c & CLS_FLOW) L |= 1u << LK::FLOW_SELF;
         if (c & CLS_ADE) L |= 1u << LK::ADE_SELF;
         if (c & CLS_SINK) L |= 1u << LK::SINK;
-        for (int i = 1; i < F::Q; ++i) {
-            if (mask_blocked<DIM>(m, x, y, z, F::c(i, 0), F::c(i, 1), F::c(i, 2), CLS_FLOW))
-                L |= 1u << i;
-        }
-        for (int i = 1; i < A::Q; ++i) {
+        for (int i = 1; i < F::Q; ++i)
+            if (mask_blocked<DIM>(m, x, y, z, F::c(i, 0), F::c(i, 1), F::c(i, 2), CLS_FLOW)) L |= 1u << i;
+        for (int i = 1; i < A::Q; ++i)
             if (mask_blocked<DIM>(m, x, y, z, A::c(i, 0), A::c(i, 1), A::c(i, 2), CLS_ADE))
                 L |= 1u << (LK::ADE_SELF + i);
-        }
         reinterpret_cast<LinkT *>(m.link)[k] = (LinkT)L;
 
         const uint8_t o = m.reset ? (uint8_t)(CLS_FLOW | CLS_ADE) : m.cls_old[q];
         const bool f_open = !(c & CLS_FLOW), a_open = !(c & CLS_ADE);
         if (f_open && (o & CLS_FLOW)) {  // opens up (or reset): flow at rest
             for (int i = 0; i < F::Q; ++i) {
-                if (m.half) reinterpret_cast<__half *>(m.fpop)[i * m.plane + k] = __float2half_rn(0.f);
-                else reinterpret_cast<float *>(m.fpop)[i * m.plane + k] = 0.f;
+                if (m.half) reinterpret_cast<__half *>(m.fpop)[i * m.geo.plane + k] = __float2half_rn(0.f);
+                else reinterpret_cast<float *>(m.fpop)[i * m.geo.plane + k] = 0.f;
             }
         }
         if (a_open && (o & CLS_ADE)) {  // opens up (or reset): no substrate
             for (int i = 0; i < A::Q; ++i) {
                 const float v = -A::w(i) * m.c_ref;
-                if (m.half) reinterpret_cast<__half *>(m.gpop)[i * m.plane + k] = __float2half_rn(v);
-                else reinterpret_cast<float *>(m.gpop)[i * m.plane + k] = v;
+                if (m.half) reinterpret_cast<__half *>(m.gpop)[i * m.geo.plane + k] = __float2half_rn(v);
+                else reinterpret_cast<float *>(m.gpop)[i * m.geo.plane + k] = v;
             }
         }
         if (m.reset || !f_open) {
             m.fld_rho[k] = 0.f;
-            for (int ax = 0; ax < DIM; ++ax) m.fld_u[ax * m.plane + k] = 0.f;
+            for (int ax = 0; ax < DIM; ++ax) m.fld_u[ax * m.geo.plane + k] = 0.f;
         }
         if (m.reset || !a_open) m.fld_c[k] = -m.c_ref;
         if (f_open) atomicAdd(&m.counts[0], 1ull);
@@ -124,9 +127,7 @@ template <int DIM> __global__ void build_links_kernel(const MaskArgs m)
     }
 }
 
-// ---- fields and populations to and from dense FP64 ------------------------------------------
-
-
+// ---- fields and populations to and from dense FP64 --------------------------------------------
 
 __device__ __forceinline__ uint32_t read_link(const void *p, int is32, long long k)
 {
@@ -135,34 +136,33 @@ __device__ __forceinline__ uint32_t read_link(const void *p, int is32, long long
 
 __global__ void fields_to_dense_kernel(const ConvArgs a)
 {
-    const long long N = (long long)a.nx * a.ny * a.nz;
+    const long long N = (long long)a.geo.nx * a.geo.ny * a.geo.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(q % a.nx);
-        const long long r = q / a.nx;
-        const long long k = x + (long long)a.px * r;
+        int x, y, z;
+        node_xyz(a.geo, q, &x, &y, &z);
+        const long long k = a.geo.at(x, y, z);
         const uint32_t L = read_link(a.link, a.link32, k);
         const bool fo = !(L & (1u << a.flow_self)), ao = !(L & (1u << a.ade_self));
         if (a.rho) a.rho[q] = fo ? 1.0 + (double)a.fld_rho[k] : 0.0;
         if (a.u)
             for (int ax = 0; ax < a.dim; ++ax)
-                a.u[ax * N + q] = fo ? (double)a.fld_u[ax * a.plane + k] : 0.0;
+                a.u[ax * N + q] = fo ? (double)a.fld_u[ax * a.geo.plane + k] : 0.0;
         if (a.c) a.c[q] = ao ? (double)(a.c_ref + a.fld_c[k]) : 0.0;
     }
 }
 
-
-
 __global__ void pop_convert_kernel(const PopArgs a)
 {
-    const long long N = (long long)a.nx * a.ny * a.nz;
+    const long long N = (long long)a.geo.nx * a.geo.ny * a.geo.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(q % a.nx);
-        const long long k = x + (long long)a.px * (q / a.nx);
+        int x, y, z;
+        node_xyz(a.geo, q, &x, &y, &z);
+        const long long k = a.geo.at(x, y, z);
         const bool open = a.self_bit < 0 || !(read_link(a.link, a.link32, k) & (1u << a.self_bit));
         for (int i = 0; i < a.q; ++i) {
-            const long long p = i * a.plane + k;
+            const long long p = i * a.geo.plane + k;
             if (a.to_dense) {
                 double v = 0.0;
                 if (open) {
@@ -180,8 +180,9 @@ __global__ void pop_convert_kernel(const PopArgs a)
     }
 }
 
-// ---- biofilm growth (simplified stand-in for the agent model of Sec. 3.3) --------------------
+// ---- biofilm growth (simplified stand-in for the agent model of Sec. 3.3) ---------------------
 
+// splitmix64 of Steele, Lea and Flood (OOPSLA 2014), as published by Vigna.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 {
     uint64_t z = x + 0x9e3779b97f4a7c15ull;
@@ -190,30 +191,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
-
-
 template <int DIM> __global__ void biofilm_grow_kernel(const GrowArgs g)
 {
     using F = FlowSet<DIM>;
-    const long long N = (long long)g.nx * g.ny * g.nz;
+    const long long N = (long long)g.geo.nx * g.geo.ny * g.geo.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
         const uint8_t c = g.cls[q];
         uint8_t out = c;
         if (c == 0) {
-            const int x = (int)(q % g.nx);
-            const int y = (int)((q / g.nx) % g.ny);
-            const int z = (int)(q / ((long long)g.nx * g.ny));
+            int x, y, z;
+            node_xyz(g.geo, q, &x, &y, &z);
             bool near = false;
 #pragma unroll
             for (int i = 1; i < F::Q; ++i) {
                 const int sx = x + F::c(i, 0), sy = y + F::c(i, 1), sz = z + F::c(i, 2);
-                if (sx < 0 || sx >= g.nx || sy < 0 || sy >= g.ny || sz < 0 || sz >= g.nz) continue;
-                if (g.cls[sx + (long long)g.nx * (sy + (long long)g.ny * sz)] & CLS_SINK) near = true;
+                if (sx < 0 || sx >= g.geo.nx || sy < 0 || sy >= g.geo.ny || sz < 0 || sz >= g.geo.nz)
+                    continue;
+                if (g.cls[sx + (long long)g.geo.nx * (sy + (long long)g.geo.ny * sz)] & CLS_SINK) near = true;
             }
             if (near) {
-                const long long k = x + (long long)g.px * (y + (long long)g.ny * z);
-                const float C = g.c_ref + g.fld_c[k];
+                const float C = g.c_ref + g.fld_c[g.geo.at(x, y, z)];
                 if ((double)C > g.c_thresh) {
                     const uint64_t h = splitmix64(g.seed ^ (g.cycle << 32) ^ (uint64_t)q);
                     if ((h >> 11) < g.lim) {

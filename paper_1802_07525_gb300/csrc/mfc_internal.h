@@ -10,15 +10,18 @@ namespace mfc {
 
 enum : int { KIND_COUPLED = 0, KIND_FLOW = 1, KIND_ADE = 2 };
 
+// Nodes per thread of the step kernels: 4 in 2-D (128-bit FP32 accesses), 2 in 3-D.
+inline int group_width(int dim) { return dim == 2 ? 4 : 2; }
+
 // Everything a step launch needs, independent of dimension and storage type.
 struct StepHost {
     int dim, half;
     int kind, mode;
-    int nx, ny, nz, px;
-    long long plane;
-    int bc_flow_axis;
-    dim3 grid, block;
-    int rows_per_block;
+    Geo geo;
+    int bc[3];
+    int gpr;
+    long long ngroups;
+    int grid, block;
     const void *fsrc;
     void *fdst;
     const void *gsrc;
@@ -33,6 +36,9 @@ struct StepHost {
 
 cudaError_t launch_step_2d(const StepHost &h, cudaStream_t s);
 cudaError_t launch_step_3d(const StepHost &h, cudaStream_t s);
+// Ghost cells of the buffers h.fdst / h.gdst from the state they hold.
+cudaError_t launch_fill_ghosts_2d(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_3d(const StepHost &h, cudaStream_t s);
 cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s);
 cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s);

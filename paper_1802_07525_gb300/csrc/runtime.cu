@@ -24,7 +24,7 @@ namespace mfc {
 
 cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s)
 {
-    const long long N = (long long)m.nx * m.ny * m.nz;
+    const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
     const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
     if (dim == 2) build_links_kernel<2><<<blocks, 256, 0, s>>>(m);
     else build_links_kernel<3><<<blocks, 256, 0, s>>>(m);
@@ -33,7 +33,7 @@ cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s)
 
 cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s)
 {
-    const long long N = (long long)g.nx * g.ny * g.nz;
+    const long long N = (long long)g.geo.nx * g.geo.ny * g.geo.nz;
     const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
     if (dim == 2) biofilm_grow_kernel<2><<<blocks, 256, 0, s>>>(g);
     else biofilm_grow_kernel<3><<<blocks, 256, 0, s>>>(g);
@@ -48,7 +48,7 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *results
 
 cudaError_t launch_fields_to_dense(const ConvArgs &a, cudaStream_t s)
 {
-    const long long N = (long long)a.nx * a.ny * a.nz;
+    const long long N = (long long)a.geo.nx * a.geo.ny * a.geo.nz;
     const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
     fields_to_dense_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -56,7 +56,7 @@ cudaError_t launch_fields_to_dense(const ConvArgs &a, cudaStream_t s)
 
 cudaError_t launch_pop_convert(const PopArgs &a, cudaStream_t s)
 {
-    const long long N = (long long)a.nx * a.ny * a.nz;
+    const long long N = (long long)a.geo.nx * a.geo.ny * a.geo.nz;
     const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
     pop_convert_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -81,8 +81,9 @@ struct mfc_lattice {
     mfc_lattice_desc desc;
     mfc_params prm;
     int dim = 2, qf = 9, qa = 5, half = 0;
-    int nx = 1, ny = 1, nz = 1, px = 32;
-    long long plane = 0, N = 0;
+    int nx = 1, ny = 1, nz = 1;
+    Geo geo;
+    long long N = 0;
     size_t st_bytes = 4;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -101,8 +102,9 @@ struct mfc_lattice {
     size_t staging_bytes = 0;
     cudaEvent_t done = nullptr;
     float c_ref = 1.0f;
-    dim3 grid, block;
-    int rows_per_block = 1, nblocks = 1;
+    int grid = 1, block = 256, nblocks = 1;
+    int gpr = 1;
+    long long ngroups = 1;
     std::vector<GraphEntry> graphs;
     long flow_open = 0, ade_open = 0;
     double last_current = 0.0;
@@ -193,42 +195,48 @@ mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
 }
 
 struct Layout {
-    int dim, qf, qa, nx, ny, nz, px;
-    long long plane, N;
+    int dim, qf, qa;
+    Geo geo;
+    long long N;
     size_t st, link_bytes;
 };
 
+// Ghost-layer layout: row pitch px = nx + 2 rounded up to 4 (left ghost of a row in the padding
+// of the row before), ghost rows y = -1 and y = ny, ghost slabs z = -1 and z = nz in 3-D, and four
+// elements in front so that node (-1, -1, -1) exists; planes rounded to 64 elements (256 B).
 Layout layout_of(const mfc_lattice_desc *d)
 {
     Layout l;
     l.dim = d->dim;
     l.qf = d->dim == 2 ? 9 : 19;
     l.qa = d->dim == 2 ? 5 : 7;
-    l.nx = d->nx;
-    l.ny = d->ny;
-    l.nz = d->dim == 2 ? 1 : d->nz;
-    l.px = (int)round_up((size_t)l.nx, 32);
-    l.plane = (long long)round_up((size_t)l.px * l.ny * l.nz, 64);
-    l.N = (long long)l.nx * l.ny * l.nz;
+    Geo &g = l.geo;
+    g.nx = d->nx;
+    g.ny = d->ny;
+    g.nz = d->dim == 2 ? 1 : d->nz;
+    g.px = (int)round_up((size_t)g.nx + 2, 4);
+    g.zs = (long long)(g.ny + 2) * g.px;
+    const int gz = d->dim == 3 ? 1 : 0;
+    g.row0 = 4 + ((long long)gz * (g.ny + 2) + 1) * g.px;
+    const long long last = g.at(0, g.ny + 1, g.nz - 1 + gz);  // first element past the last ghost row
+    g.plane = (long long)round_up((size_t)(last + 2 * g.px + 64), 64);
+    l.N = (long long)g.nx * g.ny * g.nz;
     l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
     l.link_bytes = d->dim == 2 ? 2 : 4;
     return l;
 }
 
-// Launch shape: blocks of up to 256 columns; each block walks rows_per_block rows, chosen so the
-// grid holds several waves of the 152 SMs at 8 resident blocks each.
+// Launch shape: one thread per group of nodes, blocks of 256 threads.
 void choose_launch(mfc_lattice *L)
 {
-    const int bx = L->nx >= 256 ? 256 : (int)round_up((size_t)L->nx, 32);
-    const long long gx = (L->nx + bx - 1) / bx;
-    const long long rows = (long long)L->ny * L->nz;
-    long long r = (gx * rows) / (152ll * 8 * 4);
-    if (r < 1) r = 1;
-    if (r > 16) r = 16;
-    L->block = dim3(bx, 1, 1);
-    L->rows_per_block = (int)r;
-    L->grid = dim3((unsigned)gx, (unsigned)((rows + r - 1) / r), 1);
-    L->nblocks = (int)(L->grid.x * L->grid.y);
+    const int vw = group_width(L->dim);
+    L->gpr = (L->nx + vw - 1) / vw;
+    L->ngroups = (long long)L->gpr * L->ny * L->nz;
+    L->block = 256;
+    long long b = (L->ngroups + L->block - 1) / L->block;
+    if (b > (1ll << 30)) b = 1ll << 30;
+    L->grid = (int)b;
+    L->nblocks = L->grid;
 }
 
 void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
@@ -238,11 +246,12 @@ void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->half = L->half;
     h->kind = kind;
     h->mode = mode;
-    h->nx = L->nx; h->ny = L->ny; h->nz = L->nz; h->px = L->px; h->plane = L->plane;
-    h->bc_flow_axis = L->desc.bc[L->dim == 2 ? 0 : 2];
+    h->geo = L->geo;
+    for (int a = 0; a < 3; ++a) h->bc[a] = a < L->dim ? L->desc.bc[a] : MFC_BC_PERIODIC;
+    h->gpr = L->gpr;
+    h->ngroups = L->ngroups;
     h->grid = L->grid;
     h->block = L->block;
-    h->rows_per_block = L->rows_per_block;
     h->fsrc = L->f[L->fcur];
     h->fdst = L->f[1 - L->fcur];
     h->gsrc = L->g[L->gcur];
@@ -282,6 +291,18 @@ mfc_status enqueue_step(mfc_lattice *L, int kind, int mode)
     if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     if (kind != KIND_ADE) L->fcur ^= 1;
     if (kind != KIND_FLOW) L->gcur ^= 1;
+    return MFC_OK;
+}
+
+// Rewrite the ghost cells of the current buffers from the state they hold.
+mfc_status fill_ghosts(mfc_lattice *L)
+{
+    StepHost h;
+    fill_step(L, KIND_COUPLED, MODE_PLAIN, &h);
+    h.fsrc = h.fdst = L->f[L->fcur];
+    h.gsrc = h.gdst = L->g[L->gcur];
+    cudaError_t e = L->dim == 2 ? launch_fill_ghosts_2d(h, L->stream) : launch_fill_ghosts_3d(h, L->stream);
+    if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("ghost fill: ") + cudaGetErrorString(e));
     return MFC_OK;
 }
 
@@ -456,7 +477,7 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
 {
     MaskArgs m;
     memset(&m, 0, sizeof m);
-    m.nx = L->nx; m.ny = L->ny; m.nz = L->nz; m.px = L->px; m.plane = L->plane;
+    m.geo = L->geo;
     for (int a = 0; a < 3; ++a) m.bc[a] = a < L->dim ? L->desc.bc[a] : MFC_BC_PERIODIC;
     m.cls_new = dev_cls_new;
     m.cls_old = L->cls_cur;
@@ -470,6 +491,8 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
     m.counts = L->counts_d;
     CK(L, cudaMemsetAsync(L->counts_d, 0, 2 * sizeof(unsigned long long), L->stream));
     CK(L, launch_links(L->dim, m, L->stream));
+    mfc_status st = fill_ghosts(L);
+    if (st != MFC_OK) return st;
     CK(L, cudaMemcpyAsync(L->counts_h, L->counts_d, 2 * sizeof(unsigned long long),
                           cudaMemcpyDeviceToHost, L->stream));
     CK(L, cudaStreamSynchronize(L->stream));
@@ -493,13 +516,15 @@ MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
     if (check_desc(desc, &why) != MFC_OK) return 0;
     Layout l = layout_of(desc);
     size_t b = 0;
-    b += 2 * (size_t)l.qf * l.plane * l.st;       // flow A/B
-    b += 2 * (size_t)l.qa * l.plane * l.st;       // transport A/B
-    b += (size_t)l.plane * l.link_bytes;          // links
+    const long long P = l.geo.plane;
+    b += 2 * (size_t)l.qf * P * l.st;             // flow A/B
+    b += 2 * (size_t)l.qa * P * l.st;             // transport A/B
+    b += (size_t)P * l.link_bytes;                // links
     b += 2 * round_up((size_t)l.N, 256);          // classes (current, next)
-    b += (size_t)(2 + l.dim) * l.plane * 4;       // fields
-    // partials: at most one block per 256 columns x row
-    b += (size_t)((l.nx + 255) / 256 + 1) * l.ny * l.nz * NSUM * sizeof(double);
+    b += (size_t)(2 + l.dim) * P * 4;             // fields
+    const int vw = group_width(l.dim);            // partials: one per block of 256 groups
+    const long long groups = (long long)((l.geo.nx + vw - 1) / vw) * l.geo.ny * l.geo.nz;
+    b += (size_t)((groups + 255) / 256 + 1) * NSUM * sizeof(double);
     b += 4096;
     return b;
 }
@@ -530,8 +555,9 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     L->prm = *params;
     Layout l = layout_of(desc);
     L->dim = l.dim; L->qf = l.qf; L->qa = l.qa;
-    L->nx = l.nx; L->ny = l.ny; L->nz = l.nz; L->px = l.px;
-    L->plane = l.plane; L->N = l.N;
+    L->geo = l.geo;
+    L->nx = l.geo.nx; L->ny = l.geo.ny; L->nz = l.geo.nz;
+    L->N = l.N;
     L->st_bytes = l.st;
     L->half = desc->precision == MFC_FP16_DEV;
     L->link32 = desc->dim == 3;
@@ -545,20 +571,25 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
             cudaGetLastError();
             return false;
         }
+        if (cudaMemset(*p, 0, bytes) != cudaSuccess) {  // ghosts and padding start defined
+            cudaGetLastError();
+            return false;
+        }
         L->bytes += bytes;
         return true;
     };
+    const long long P = l.geo.plane;
     bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {
-        ok = ok && dalloc(&L->f[b], (size_t)l.qf * l.plane * l.st);
-        ok = ok && dalloc(&L->g[b], (size_t)l.qa * l.plane * l.st);
+        ok = ok && dalloc(&L->f[b], (size_t)l.qf * P * l.st);
+        ok = ok && dalloc(&L->g[b], (size_t)l.qa * P * l.st);
     }
-    ok = ok && dalloc(&L->link, (size_t)l.plane * l.link_bytes);
+    ok = ok && dalloc(&L->link, (size_t)P * l.link_bytes);
     ok = ok && dalloc((void **)&L->cls_cur, round_up((size_t)l.N, 256));
     ok = ok && dalloc((void **)&L->cls_tmp, round_up((size_t)l.N, 256));
-    ok = ok && dalloc((void **)&L->fld_rho, (size_t)l.plane * 4);
-    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * l.plane * 4);
-    ok = ok && dalloc((void **)&L->fld_c, (size_t)l.plane * 4);
+    ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
+    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
+    ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
     ok = ok && dalloc((void **)&L->partials, (size_t)L->nblocks * NSUM * sizeof(double));
     ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
     ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
@@ -626,7 +657,7 @@ MFC_API mfc_status mfc_set_params(mfc_lattice *L, const mfc_params *params)
     if (st != MFC_OK) return fail(L, st, why);
     L->prm = *params;
     drop_graphs(L);  // the graphs hold the old constants
-    return MFC_OK;
+    return fill_ghosts(L);  // inlet and outlet ghost values depend on the parameters
 }
 
 MFC_API mfc_status mfc_set_geometry(mfc_lattice *L, const uint8_t *node_class, int reset_fields)
@@ -702,7 +733,7 @@ MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *L, uint64_t seed, uint64_t cycl
         return fail(L, MFC_ERR_ARG, "prob must be in [0,1], c_thresh finite");
     GrowArgs g;
     memset(&g, 0, sizeof g);
-    g.nx = L->nx; g.ny = L->ny; g.nz = L->nz; g.px = L->px;
+    g.geo = L->geo;
     g.cls = L->cls_cur;
     g.cls_out = L->cls_tmp;
     g.fld_c = L->fld_c;
@@ -733,7 +764,8 @@ MFC_API mfc_status mfc_read_fields(mfc_lattice *L, double *rho, double *u, doubl
     if (st != MFC_OK) return st;
     ConvArgs a;
     memset(&a, 0, sizeof a);
-    a.nx = L->nx; a.ny = L->ny; a.nz = L->nz; a.px = L->px; a.dim = L->dim; a.plane = L->plane;
+    a.geo = L->geo;
+    a.dim = L->dim;
     a.link = L->link;
     a.link32 = L->link32;
     a.flow_self = 0;
@@ -761,7 +793,7 @@ static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const doub
     if (!host_out && !host_in) return fail(L, MFC_ERR_ARG, "host buffer is NULL");
     PopArgs a;
     memset(&a, 0, sizeof a);
-    a.nx = L->nx; a.ny = L->ny; a.nz = L->nz; a.px = L->px; a.plane = L->plane;
+    a.geo = L->geo;
     a.link = L->link;
     a.link32 = L->link32;
     if (which == MFC_POP_FLOW) {
@@ -795,6 +827,10 @@ static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const doub
     if (host_in) CK(L, cudaMemcpyAsync(L->staging, host_in, bytes, cudaMemcpyHostToDevice, L->stream));
     CK(L, launch_pop_convert(a, L->stream));
     if (host_out) CK(L, cudaMemcpyAsync(host_out, L->staging, bytes, cudaMemcpyDeviceToHost, L->stream));
+    if (host_in && which != MFC_FIELD_VELOCITY) {
+        st = fill_ghosts(L);
+        if (st != MFC_OK) return st;
+    }
     CK(L, cudaStreamSynchronize(L->stream));
     return MFC_OK;
 }
