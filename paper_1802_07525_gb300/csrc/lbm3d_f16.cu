@@ -1,0 +1,6 @@
+// 3-D step and ghost-fill kernels with FP16 population storage.
+#define MFC_DIM 3
+#define MFC_ST __half
+#define MFC_STEP_FN launch_step_3d_f16
+#define MFC_FILL_FN launch_fill_ghosts_3d_f16
+#include "lbm_launch.cuh"

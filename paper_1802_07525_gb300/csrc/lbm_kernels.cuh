@@ -16,10 +16,11 @@
 // the outlet are realised by the boundary nodes writing, after their collision, the values their
 // readers must see into the ghost cells of the buffer the next step reads.
 //
-// Threads.  One thread updates VW consecutive nodes of a row (VW = 4 in 2-D, 2 in 3-D) with
-// 128-bit (64-bit) loads and stores.  The populations that move along x come from the
-// neighbouring lane's vector through a warp shuffle; the first or last lane of a warp, and a
-// group at the start or end of a row, loads that one element itself.
+// Threads.  One thread updates VW consecutive nodes of a row (VW = 4 in 2-D, 2 in 3-D by
+// default) with 128-bit (64-bit) loads and stores; the grid is (groups of a row / block, ny, nz),
+// so no index needs a division.  The populations that move along x come from the neighbouring
+// lane's vector through a warp shuffle; the first or last lane of a warp, and a group at the
+// start or end of a row, loads that one element itself.
 //
 // Precision.  Flow populations are stored as deviations from rest (f_i - w_i), transport ones
 // as g_i - w_i c_ref; FP32 or FP16 storage, FP32 arithmetic.  The rest population of each lattice
@@ -54,8 +55,7 @@ template <int DIM, typename ST> struct StepArgs {
 
     Geo geo;
     int bc[3];            // boundary kind per axis
-    int gpr;              // node groups per row = ceil(nx / VW)
-    long long ngroups;    // gpr * ny * nz
+    int gpr;              // node groups per row = ceil(nx / VW); grid = (groups / block, ny, nz)
     const ST *fsrc;       // flow populations, previous step, QF planes
     ST *fdst;             // flow populations, this step
     const ST *gsrc;       // transport populations, previous step, QA planes
@@ -83,7 +83,9 @@ template <int DIM> __host__ __device__ constexpr int flow_axis() { return DIM ==
 
 template <int VW> __device__ __forceinline__ void ldv(const float *p, float (&v)[VW])
 {
-    if constexpr (VW == 4) {
+    if constexpr (VW == 1) {
+        v[0] = __ldg(p);
+    } else if constexpr (VW == 4) {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     } else {
@@ -94,7 +96,9 @@ template <int VW> __device__ __forceinline__ void ldv(const float *p, float (&v)
 
 template <int VW> __device__ __forceinline__ void ldv(const __half *p, float (&v)[VW])
 {
-    if constexpr (VW == 4) {
+    if constexpr (VW == 1) {
+        v[0] = __half2float(__ldg(p));
+    } else if constexpr (VW == 4) {
         const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
@@ -108,13 +112,16 @@ template <int VW> __device__ __forceinline__ void ldv(const __half *p, float (&v
 
 template <int VW> __device__ __forceinline__ void stv(float *p, const float (&v)[VW])
 {
-    if constexpr (VW == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    if constexpr (VW == 1) *p = v[0];
+    else if constexpr (VW == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
 }
 
 template <int VW> __device__ __forceinline__ void stv(__half *p, const float (&v)[VW])
 {
-    if constexpr (VW == 4) {
+    if constexpr (VW == 1) {
+        *p = __float2half_rn(v[0]);
+    } else if constexpr (VW == 4) {
         __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
         uint2 t;
         t.x = *reinterpret_cast<unsigned *>(&a);
@@ -130,7 +137,9 @@ template <int VW> __device__ __forceinline__ void stv(__half *p, const float (&v
 template <int VW, typename LinkT>
 __device__ __forceinline__ void ld_links(const LinkT *p, uint32_t (&L)[VW])
 {
-    if constexpr (sizeof(LinkT) == 2 && VW == 4) {
+    if constexpr (VW == 1) {
+        L[0] = __ldg(p);
+    } else if constexpr (sizeof(LinkT) == 2 && VW == 4) {
         const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
         L[0] = t.x & 0xffffu; L[1] = t.x >> 16; L[2] = t.y & 0xffffu; L[3] = t.y >> 16;
     } else if constexpr (sizeof(LinkT) == 2 && VW == 2) {
@@ -185,6 +194,26 @@ __device__ __forceinline__ void gather(const ST *p_row, int cx, bool own_left, b
     }
 }
 
+// The node group's own populations of the opposite plane, for bounce-back along bit `bit`.
+template <int VW, int BB, typename ST>
+__device__ __forceinline__ void own_opposite(const ST *p, const uint32_t (&L)[VW], int bit,
+                                             float (&own)[VW])
+{
+    if (BB == 0) {
+        ldv<VW>(p, own);
+    } else {
+        uint32_t any = 0;
+#pragma unroll
+        for (int j = 0; j < VW; ++j) any |= (L[j] >> bit) & 1u;
+        if (any) {
+            ldv<VW>(p, own);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VW; ++j) own[j] = 0.f;
+        }
+    }
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
@@ -210,7 +239,8 @@ __device__ __forceinline__ void block_partials(double (&acc)[NSUM], double *part
         for (int m = 0; m < NSUM; ++m) {
             double v = lane < nwarp ? sh[lane][m] : 0.0;
             v = warp_sum(v);
-            if (lane == 0) partials[(size_t)blockIdx.x * NSUM + m] = v;
+            if (lane == 0)
+                partials[((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)) * NSUM + m] = v;
         }
     }
 }
@@ -336,7 +366,11 @@ __device__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, in
 
 // ---- the step kernel -------------------------------------------------------------------------
 
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int VW>
+// Launch variants (chosen per lattice, the results are identical bit for bit):
+//   VW  nodes per thread (1, 2 or 4);
+//   BB  0: the own opposite populations are loaded for every direction, independent of the link
+//       word (no load waits on another); 1: only when a node of the group bounces back.
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int VW, int BB>
 __global__ void __launch_bounds__(256) lbm_step_kernel(const StepArgs<DIM, ST> a)
 {
     using F = FlowSet<DIM>;
@@ -348,15 +382,12 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const StepArgs<DIM, ST> a
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
 
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long gb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); gb < a.ngroups;
-         gb += stride) {
-        long long gi = gb + lane;
-        const bool live = gi < a.ngroups;
-        if (!live) gi = a.ngroups - 1;  // a copy of a live group keeps the shuffles defined
-        const long long r = gi / a.gpr;
-        const int x0 = VW * (int)(gi - r * a.gpr);
-        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    {
+        const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+        const int y = blockIdx.y, z = blockIdx.z;
+        const bool live = gx < a.gpr;
+        // lanes past the end of the row repeat the last group, which keeps the shuffles defined
+        const int x0 = VW * (live ? gx : a.gpr - 1);
         const long long k0 = g.at(x0, y, z);
         const int nvalid = live ? min(VW, g.nx - x0) : 0;
         const bool full = nvalid == VW;
@@ -380,7 +411,7 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const StepArgs<DIM, ST> a
                 const long long ks = k0 - ((long long)F::c(i, 1) * g.px + (long long)F::c(i, 2) * g.zs);
                 float src[VW], own[VW];
                 gather<VW>(a.fsrc + (long long)i * g.plane + ks, F::c(i, 0), own_left, own_right, src);
-                ldv<VW>(a.fsrc + (long long)F::opp(i) * g.plane + k0, own);
+                own_opposite<VW, BB>(a.fsrc + (long long)F::opp(i) * g.plane + k0, L, i, own);
 #pragma unroll
                 for (int j = 0; j < VW; ++j) d[i][j] = ((L[j] >> i) & 1u) ? own[j] : src[j];
             }
@@ -497,7 +528,7 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const StepArgs<DIM, ST> a
                 const long long ks = k0 - ((long long)A::c(i, 1) * g.px + (long long)A::c(i, 2) * g.zs);
                 float src[VW], own[VW];
                 gather<VW>(a.gsrc + (long long)i * g.plane + ks, A::c(i, 0), own_left, own_right, src);
-                ldv<VW>(a.gsrc + (long long)A::opp(i) * g.plane + k0, own);
+                own_opposite<VW, BB>(a.gsrc + (long long)A::opp(i) * g.plane + k0, L, LK::ADE_SELF + i, own);
 #pragma unroll
                 for (int j = 0; j < VW; ++j) e[i][j] = ((L[j] >> (LK::ADE_SELF + i)) & 1u) ? own[j] : src[j];
             }

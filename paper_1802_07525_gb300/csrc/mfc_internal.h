@@ -10,8 +10,10 @@ namespace mfc {
 
 enum : int { KIND_COUPLED = 0, KIND_FLOW = 1, KIND_ADE = 2 };
 
-// Nodes per thread of the step kernels: 4 in 2-D (128-bit FP32 accesses), 2 in 3-D.
-inline int group_width(int dim) { return dim == 2 ? 4 : 2; }
+// Default launch variant of the step kernels: nodes per thread (4 in 2-D: 128-bit FP32
+// accesses; 2 in 3-D), own-opposite load mode, threads per block.
+inline int default_vw(int dim) { return dim == 2 ? 4 : 2; }
+enum : int { DEFAULT_BB = 0, DEFAULT_BLOCK = 256 };
 
 // Everything a step launch needs, independent of dimension and storage type.
 struct StepHost {
@@ -19,6 +21,10 @@ struct StepHost {
     int kind, mode;
     Geo geo;
     int bc[3];
+    int vw, bb;       // launch variant: nodes per thread, own-opposite load mode
+    int staged;       // 1: TMA-staged kernel (2-D), block threads = strip width
+    int *err;         // pipeline error flag (staged kernel)
+    int nblocks;      // out: blocks of the launch (one reduction partial each)
     int gpr;
     long long ngroups;
     int grid, block;
@@ -34,11 +40,32 @@ struct StepHost {
     float bb_in[19], gin_dev[7], gout_dev[7];
 };
 
-cudaError_t launch_step_2d(const StepHost &h, cudaStream_t s);
-cudaError_t launch_step_3d(const StepHost &h, cudaStream_t s);
+cudaError_t launch_step_2d_f32(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_2d_f16(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_3d_f32(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_3d_f16(StepHost &h, cudaStream_t s);
 // Ghost cells of the buffers h.fdst / h.gdst from the state they hold.
-cudaError_t launch_fill_ghosts_2d(const StepHost &h, cudaStream_t s);
-cudaError_t launch_fill_ghosts_3d(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d_f32(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d_f16(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_3d_f32(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_3d_f16(const StepHost &h, cudaStream_t s);
+
+// Staged-kernel plan: strips of h.block columns, segments of seg_rows rows, sized from the
+// occupancy of the kernel so that one wave covers the lattice.
+void staged_plan_2d_f32(const StepHost &h, int *nstrips, int *seg_rows);
+void staged_plan_2d_f16(const StepHost &h, int *nstrips, int *seg_rows);
+
+inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
+{
+    if (h.dim == 2) return h.half ? launch_step_2d_f16(h, s) : launch_step_2d_f32(h, s);
+    return h.half ? launch_step_3d_f16(h, s) : launch_step_3d_f32(h, s);
+}
+
+inline cudaError_t launch_fill_ghosts(const StepHost &h, cudaStream_t s)
+{
+    if (h.dim == 2) return h.half ? launch_fill_ghosts_2d_f16(h, s) : launch_fill_ghosts_2d_f32(h, s);
+    return h.half ? launch_fill_ghosts_3d_f16(h, s) : launch_fill_ghosts_3d_f32(h, s);
+}
 cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s);
 cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s);

@@ -102,7 +102,9 @@ struct mfc_lattice {
     size_t staging_bytes = 0;
     cudaEvent_t done = nullptr;
     float c_ref = 1.0f;
-    int grid = 1, block = 256, nblocks = 1;
+    int grid = 1, block = DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
+    int vw = 4, bb = DEFAULT_BB, staged = 0;
+    int *err_d = nullptr;  // pipeline error flag, lives after the results
     int gpr = 1;
     long long ngroups = 1;
     std::vector<GraphEntry> graphs;
@@ -174,7 +176,10 @@ mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
     if (d->dim != 2 && d->dim != 3) { *why = "dim must be 2 or 3"; return MFC_ERR_ARG; }
     const int nz = d->dim == 2 ? 1 : d->nz;
     if (d->nx < 1 || d->ny < 1 || nz < 1) { *why = "sizes must be >= 1"; return MFC_ERR_ARG; }
-    if ((long long)d->nx * d->ny * nz > (1ll << 33)) { *why = "lattice too large"; return MFC_ERR_ARG; }
+    if ((long long)d->nx * d->ny * nz > (1ll << 31) || d->ny > 65535 || nz > 65535) {
+        *why = "lattice too large (at most 2^31 nodes, ny and nz at most 65535)";
+        return MFC_ERR_ARG;
+    }
     const int fa = d->dim == 2 ? 0 : 2;
     for (int a = 0; a < d->dim; ++a) {
         const int b = d->bc[a];
@@ -214,29 +219,36 @@ Layout layout_of(const mfc_lattice_desc *d)
     g.nx = d->nx;
     g.ny = d->ny;
     g.nz = d->dim == 2 ? 1 : d->nz;
-    g.px = (int)round_up((size_t)g.nx + 2, 4);
+    // pitch and front offset are multiples of 8 elements, so that 16-byte bulk copies of
+    // FP16 rows (and of 16-bit link rows) start aligned
+    g.px = (int)round_up((size_t)g.nx + 2, 8);
     g.zs = (long long)(g.ny + 2) * g.px;
     const int gz = d->dim == 3 ? 1 : 0;
-    g.row0 = 4 + ((long long)gz * (g.ny + 2) + 1) * g.px;
+    g.row0 = 8 + ((long long)gz * (g.ny + 2) + 1) * g.px;
     const long long last = g.at(0, g.ny + 1, g.nz - 1 + gz);  // first element past the last ghost row
-    g.plane = (long long)round_up((size_t)(last + 2 * g.px + 64), 64);
+    // slack for the widest staged copy of the last ghost row (a strip of up to 256 + halo)
+    g.plane = (long long)round_up((size_t)(last + 2 * g.px + 512 + 64), 64);
     l.N = (long long)g.nx * g.ny * g.nz;
     l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
     l.link_bytes = d->dim == 2 ? 2 : 4;
     return l;
 }
 
-// Launch shape: one thread per group of nodes, blocks of 256 threads.
+// Launch shape of a variant: one thread per group of vw nodes of a row, grid (groups of a row /
+// block, ny, nz).
 void choose_launch(mfc_lattice *L)
 {
-    const int vw = group_width(L->dim);
-    L->gpr = (L->nx + vw - 1) / vw;
+    L->gpr = (L->nx + L->vw - 1) / L->vw;
     L->ngroups = (long long)L->gpr * L->ny * L->nz;
-    L->block = 256;
-    long long b = (L->ngroups + L->block - 1) / L->block;
-    if (b > (1ll << 30)) b = 1ll << 30;
-    L->grid = (int)b;
-    L->nblocks = L->grid;
+    L->grid = (L->gpr + L->block - 1) / L->block;
+    L->nblocks = L->grid * L->ny * L->nz;
+}
+
+// Blocks of the largest launch any variant makes (one node per thread, 128 threads per block):
+// the size of the partial-sum buffer.
+int max_launch_blocks(const Layout &l)
+{
+    return (l.geo.nx + 127) / 128 * l.geo.ny * l.geo.nz;
 }
 
 void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
@@ -248,6 +260,10 @@ void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->mode = mode;
     h->geo = L->geo;
     for (int a = 0; a < 3; ++a) h->bc[a] = a < L->dim ? L->desc.bc[a] : MFC_BC_PERIODIC;
+    h->vw = L->vw;
+    h->bb = L->bb;
+    h->staged = L->staged;
+    h->err = L->err_d;
     h->gpr = L->gpr;
     h->ngroups = L->ngroups;
     h->grid = L->grid;
@@ -282,13 +298,15 @@ void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     }
 }
 
-// Queue one step of `kind` and swap the buffers it wrote.
-mfc_status enqueue_step(mfc_lattice *L, int kind, int mode)
+// Queue one step of `kind` and swap the buffers it wrote; *nblocks receives the blocks (and
+// reduction partials) of the launch.
+mfc_status enqueue_step(mfc_lattice *L, int kind, int mode, int *nblocks = nullptr)
 {
     StepHost h;
     fill_step(L, kind, mode, &h);
-    cudaError_t e = L->dim == 2 ? launch_step_2d(h, L->stream) : launch_step_3d(h, L->stream);
+    cudaError_t e = launch_step(h, L->stream);
     if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    if (nblocks) *nblocks = h.nblocks;
     if (kind != KIND_ADE) L->fcur ^= 1;
     if (kind != KIND_FLOW) L->gcur ^= 1;
     return MFC_OK;
@@ -301,7 +319,7 @@ mfc_status fill_ghosts(mfc_lattice *L)
     fill_step(L, KIND_COUPLED, MODE_PLAIN, &h);
     h.fsrc = h.fdst = L->f[L->fcur];
     h.gsrc = h.gdst = L->g[L->gcur];
-    cudaError_t e = L->dim == 2 ? launch_fill_ghosts_2d(h, L->stream) : launch_fill_ghosts_3d(h, L->stream);
+    cudaError_t e = launch_fill_ghosts(h, L->stream);
     if (e != cudaSuccess) return fail(L, MFC_ERR_CUDA, std::string("ghost fill: ") + cudaGetErrorString(e));
     return MFC_OK;
 }
@@ -309,16 +327,18 @@ mfc_status fill_ghosts(mfc_lattice *L)
 // Queue n steps ending with a residual check (n >= 2) or with a field store (n == 1).
 mfc_status enqueue_block(mfc_lattice *L, int kind, int n, bool check)
 {
+    int nb = L->nblocks;
     for (int s = 0; s < n; ++s) {
         int mode = MODE_PLAIN;
         if (s == n - 1) mode = check ? MODE_CHECK : MODE_WRITE;
         else if (s == n - 2 && check) mode = MODE_WRITE;
-        mfc_status st = enqueue_step(L, kind, mode);
+        mfc_status st = enqueue_step(L, kind, mode, &nb);
         if (st != MFC_OK) return st;
     }
     if (check) {
-        CK(L, launch_finalize(L->partials, L->nblocks, L->results_d, L->stream));
-        CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * NRESULT,
+        CK(L, launch_finalize(L->partials, nb, L->results_d, L->stream));
+        // the results and, after them, the pipeline error flag
+        CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * (NRESULT + 1),
                               cudaMemcpyDeviceToHost, L->stream));
     }
     return MFC_OK;
@@ -415,6 +435,8 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
         *steps += n;
         if (n >= 2) {
             const double *r = L->results_h;
+            if (*reinterpret_cast<const int *>(r + NRESULT) != 0)
+                return fail(L, MFC_ERR_CUDA, "a staged copy did not complete within the wait limit");
             if (kind != KIND_ADE) *res_f = r[RES_FLOW];
             if (kind != KIND_FLOW) {
                 *res_a = r[RES_ADE];
@@ -522,9 +544,7 @@ MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
     b += (size_t)P * l.link_bytes;                // links
     b += 2 * round_up((size_t)l.N, 256);          // classes (current, next)
     b += (size_t)(2 + l.dim) * P * 4;             // fields
-    const int vw = group_width(l.dim);            // partials: one per block of 256 groups
-    const long long groups = (long long)((l.geo.nx + vw - 1) / vw) * l.geo.ny * l.geo.nz;
-    b += (size_t)((groups + 255) / 256 + 1) * NSUM * sizeof(double);
+    b += (size_t)max_launch_blocks(l) * NSUM * sizeof(double);  // partials
     b += 4096;
     return b;
 }
@@ -564,6 +584,10 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     // transport storage offset: 0, so that the no-substrate start state is stored exactly
     L->c_ref = 0.0f;
     cudaGetDevice(&L->device);
+    L->vw = default_vw(L->dim);
+    L->bb = DEFAULT_BB;
+    L->block = DEFAULT_BLOCK;
+    L->max_blocks = max_launch_blocks(l);
     choose_launch(L);
 
     auto dalloc = [&](void **p, size_t bytes) -> bool {
@@ -590,15 +614,16 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
     ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
     ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
-    ok = ok && dalloc((void **)&L->partials, (size_t)L->nblocks * NSUM * sizeof(double));
-    ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
+    ok = ok && dalloc((void **)&L->partials, (size_t)L->max_blocks * NSUM * sizeof(double));
+    ok = ok && dalloc((void **)&L->results_d, (NRESULT + 1) * sizeof(double));
     ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
     if (!ok) {
         release(L);
         delete L;
         return fail(nullptr, MFC_ERR_OOM, "device allocation failed");
     }
-    cudaError_t e = cudaHostAlloc((void **)&L->results_h, NRESULT * sizeof(double), cudaHostAllocDefault);
+    L->err_d = reinterpret_cast<int *>(L->results_d + NRESULT);
+    cudaError_t e = cudaHostAlloc((void **)&L->results_h, (NRESULT + 1) * sizeof(double), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&L->counts_h, 2 * sizeof(unsigned long long), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
     if (e == cudaSuccess) {
@@ -615,7 +640,7 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
         delete L;
         return fail(nullptr, MFC_ERR_CUDA, msg);
     }
-    memset(L->results_h, 0, NRESULT * sizeof(double));
+    memset(L->results_h, 0, (NRESULT + 1) * sizeof(double));
     // every node open, rest state
     e = cudaMemsetAsync(L->cls_cur, 0, round_up((size_t)l.N, 256), L->stream);
     if (e != cudaSuccess) {
@@ -850,6 +875,38 @@ MFC_API mfc_status mfc_synchronize(mfc_lattice *L)
     mfc_status st = enter(L);
     if (st != MFC_OK) return st;
     CK(L, cudaStreamSynchronize(L->stream));
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_set_launch(mfc_lattice *L, const mfc_launch *v)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!v) return fail(L, MFC_ERR_ARG, "launch is NULL");
+    const bool vw_ok = v->nodes_per_thread == 1 || v->nodes_per_thread == 2 ||
+                       (v->nodes_per_thread == 4 && L->dim == 2);
+    const bool blk_ok = v->block == 128 || v->block == 256;
+    const bool st_ok = v->staged == 0 || (v->staged == 1 && L->dim == 2);
+    if (!vw_ok || !blk_ok || !st_ok || (v->bounce_loads != 0 && v->bounce_loads != 1))
+        return fail(L, MFC_ERR_ARG, "launch variant not available (nodes_per_thread 1|2|4 (4 in 2-D), "
+                                    "bounce_loads 0|1, block 128|256, staged 0|1 (1 in 2-D))");
+    CK(L, cudaStreamSynchronize(L->stream));
+    L->vw = v->nodes_per_thread;
+    L->bb = v->bounce_loads;
+    L->block = v->block;
+    L->staged = v->staged;
+    choose_launch(L);
+    drop_graphs(L);
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_get_launch(mfc_lattice *L, mfc_launch *v)
+{
+    if (!L || !v) return MFC_ERR_ARG;
+    v->nodes_per_thread = L->vw;
+    v->bounce_loads = L->bb;
+    v->block = L->block;
+    v->staged = L->staged;
     return MFC_OK;
 }
 

@@ -58,6 +58,14 @@ class SolveResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Launch(ctypes.Structure):
+    _fields_ = [("nodes_per_thread", ctypes.c_int), ("bounce_loads", ctypes.c_int),
+                ("block", ctypes.c_int), ("staged", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MfcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_string(status)} ({status}): {msg}")
@@ -85,6 +93,8 @@ _SIGS = {
     "mfc_read_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "mfc_write_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "mfc_synchronize": (ctypes.c_int, [_vp]),
+    "mfc_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
+    "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_active_nodes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_long),
                                         ctypes.POINTER(ctypes.c_long)]),
     "mfc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -249,6 +259,15 @@ class Lattice:
         q = {MFC_POP_FLOW: self.qf, MFC_POP_ADE: self.qa, MFC_FIELD_VELOCITY: self.dim}[which]
         v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(q, self.N))
         self._check(self._L.mfc_write_populations(self.handle, which, _ptr(v)))
+
+    def set_launch(self, nodes_per_thread=1, bounce_loads=0, block=256, staged=0):
+        v = Launch(int(nodes_per_thread), int(bounce_loads), int(block), int(staged))
+        self._check(self._L.mfc_set_launch(self.handle, ctypes.byref(v)))
+
+    def get_launch(self) -> dict:
+        v = Launch()
+        self._check(self._L.mfc_get_launch(self.handle, ctypes.byref(v)))
+        return v.as_dict()
 
     def synchronize(self):
         self._check(self._L.mfc_synchronize(self.handle))

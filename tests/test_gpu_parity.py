@@ -320,3 +320,68 @@ def test_fp16_deviation_storage_error_is_bounded(P):
           f"max |f - f_oracle| {maxabs(g.read_populations(P.MFC_POP_FLOW), o.f):.3e}")
     assert eu < 2e-2
     assert ec < 1e-2
+
+
+# ------------------------------------------------------------------------------------------
+# Launch variants: every variant computes the same result bit for bit
+# ------------------------------------------------------------------------------------------
+
+def _variants(dim):
+    out = []
+    for vw in ((1, 2, 4) if dim == 2 else (1, 2)):
+        for bb in (0, 1):
+            for blk in (128, 256):
+                out.append(dict(nodes_per_thread=vw, bounce_loads=bb, block=blk, staged=0))
+    if dim == 2:
+        for blk in (128, 256):
+            out.append(dict(nodes_per_thread=1, bounce_loads=0, block=blk, staged=1))
+    return out
+
+
+@pytest.mark.parametrize("shape,bc,prec", [
+    ((300, 37), (2, 0), 0),      # ragged strip and row tails, inlet/outlet, walls
+    ((133, 20), (2, 1), 0),      # periodic cross axis
+    ((64, 24), (1, 1), 0),       # fully periodic
+    ((45, 9), (0, 0), 0),        # closed box
+    ((300, 37), (2, 0), 1),      # FP16 storage
+    ((23, 11, 17), (0, 0, 2), 0),
+    ((16, 9, 10), (1, 1, 1), 0),
+])
+def test_launch_variants_are_bitwise_identical(P, shape, bc, prec):
+    dim = len(shape)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N + prec)
+    r = rng.random(N)
+    cls = np.where(r < 0.15, 3, np.where(r < 0.3, 4, np.where(r < 0.35, 5, 0))).astype(np.uint8)
+    kw = dict(tau=0.7, tau_c=0.9, u_in=0.03, c_in=0.8, k_sink=0.01)
+    f0 = g0 = None
+    if bc[0] != 2 and (dim == 2 or bc[2] != 2):
+        o = oracle.Oracle(shape, cls, bc=bc, **kw)
+        for k in np.nonzero((cls & 1) == 0)[0]:
+            o.f[:, k] = oracle.flow_equilibrium(dim, 1.0 + 0.01 * rng.standard_normal(),
+                                                0.02 * rng.standard_normal(dim))
+        f0 = o.f.copy()
+        g0 = np.where((cls & 2) == 0, rng.random((o.qa, N)) * 0.2, 0.0)
+    ref = None
+    for v in _variants(dim):
+        g = P.Lattice(shape, bc=bc, precision=prec, **kw)
+        g.set_geometry(cls)
+        g.set_launch(**v)
+        if f0 is not None:
+            g.write_populations(P.MFC_POP_FLOW, f0)
+            g.write_populations(P.MFC_POP_ADE, g0)
+        g.step_coupled(37)
+        r1 = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=6, check_every=6)
+        g.step_flow(5)
+        g.step_ade(4)
+        out = (g.read_populations(P.MFC_POP_FLOW), g.read_populations(P.MFC_POP_ADE),
+               g.read_fields()[1], (r1.res_flow, r1.res_ade, r1.current, r1.mass))
+        g.close()
+        if ref is None:
+            ref = out
+            continue
+        assert np.array_equal(out[0], ref[0]), v
+        assert np.array_equal(out[1], ref[1]), v
+        assert np.array_equal(out[2], ref[2]), v
+        # partial sums are added in a block order that depends on the launch shape
+        assert np.allclose(out[3], ref[3], rtol=1e-12, atol=0), v
