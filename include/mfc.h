@@ -178,23 +178,13 @@ MFC_API mfc_status mfc_synchronize(mfc_lattice *lat);
 
 /* ---- launch variants ---------------------------------------------------------------------- */
 
-/* How the step kernel is launched; every variant computes the same result bit for bit.
- * staged = 0: each thread gathers its populations from global memory.
- *   nodes_per_thread: 1, 2 or 4 (4 in 2-D only) consecutive nodes of a row per thread;
- *   bounce_loads: 0 loads each node group's own opposite populations for every direction (no
- *   load waits on the link word), 1 only where a node of the group bounces back;
- *   block: 128 or 256 threads.
- * staged = 1 (2-D only): a CTA of `block` (128 or 256) threads sweeps a strip of that many
- *   columns down a segment of rows, with the rows it needs copied ahead into shared memory by
- *   bulk asynchronous copies (TMA); nodes_per_thread and bounce_loads are ignored. */
+/* How the step kernel is launched: one thread per node, `block` (128 or 256) threads along a
+ * row per block.  Every choice computes the same arithmetic. */
 typedef struct {
-    int nodes_per_thread;
-    int bounce_loads;
     int block;
-    int staged;
 } mfc_launch;
 
-/* Select the launch variant (waits for queued work; captured step graphs are rebuilt). */
+/* Select the launch shape (waits for queued work; captured step graphs are rebuilt). */
 MFC_API mfc_status mfc_set_launch(mfc_lattice *lat, const mfc_launch *launch);
 MFC_API mfc_status mfc_get_launch(mfc_lattice *lat, mfc_launch *launch);
 

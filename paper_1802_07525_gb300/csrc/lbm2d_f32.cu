@@ -3,5 +3,4 @@
 #define MFC_ST float
 #define MFC_STEP_FN launch_step_2d_f32
 #define MFC_FILL_FN launch_fill_ghosts_2d_f32
-#define MFC_PLAN_FN staged_plan_2d_f32
 #include "lbm_launch.cuh"

@@ -10,17 +10,18 @@
 //
 // Layout.  Every population plane, link word and field uses one pitched layout with a ghost
 // layer around the lattice: node (x, y, z), x in [-1, nx], y in [-1, ny], z in [-1, nz] (3-D),
-// sits at row0 + z*zs + y*px + x.  The row pitch px (a multiple of 4, >= nx + 2) keeps the left
-// ghost of a row in the padding of the row before it, so every pull is a literal, in-bounds
-// address and the interior needs no boundary branches.  Periodic axes, the moving-wall inlet and
-// the outlet are realised by the boundary nodes writing, after their collision, the values their
-// readers must see into the ghost cells of the buffer the next step reads.
+// sits at row0 + z*zs + y*px + x.  The row pitch px (>= nx + 2) keeps the left ghost of a row in
+// the padding of the row before it, so every pull is a literal, in-bounds address and the
+// interior needs no boundary branches.  Periodic axes, the moving-wall inlet and the outlet are
+// realised by the boundary nodes writing, after their collision, the values their readers must
+// see into the ghost cells of the buffer the next step reads; only blocks that touch such a
+// boundary look at it.
 //
-// Threads.  One thread updates VW consecutive nodes of a row (VW = 4 in 2-D, 2 in 3-D by
-// default) with 128-bit (64-bit) loads and stores; the grid is (groups of a row / block, ny, nz),
-// so no index needs a division.  The populations that move along x come from the neighbouring
-// lane's vector through a warp shuffle; the first or last lane of a warp, and a group at the
-// start or end of a row, loads that one element itself.
+// Threads.  One thread per node; the grid is (row / block, ny, nz), so no index needs a
+// division.  Each thread issues all its loads up front: the regular pull of every direction and
+// the own opposite population (bounce-back) unconditionally, selected by the link bits, so no
+// load waits on another.  Every node of a row is stored, blocked ones with their zeros, so the
+// stores cover whole 32-byte sectors.
 //
 // Precision.  Flow populations are stored as deviations from rest (f_i - w_i), transport ones
 // as g_i - w_i c_ref; FP32 or FP16 storage, FP32 arithmetic.  The rest population of each lattice
@@ -55,7 +56,6 @@ template <int DIM, typename ST> struct StepArgs {
 
     Geo geo;
     int bc[3];            // boundary kind per axis
-    int gpr;              // node groups per row = ceil(nx / VW); grid = (groups / block, ny, nz)
     const ST *fsrc;       // flow populations, previous step, QF planes
     ST *fdst;             // flow populations, this step
     const ST *gsrc;       // transport populations, previous step, QA planes
@@ -79,140 +79,9 @@ template <int DIM, typename ST> struct StepArgs {
 
 template <int DIM> __host__ __device__ constexpr int flow_axis() { return DIM == 2 ? 0 : 2; }
 
-// ---- vector loads and stores -----------------------------------------------------------------
-
-template <int VW> __device__ __forceinline__ void ldv(const float *p, float (&v)[VW])
-{
-    if constexpr (VW == 1) {
-        v[0] = __ldg(p);
-    } else if constexpr (VW == 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else {
-        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-        v[0] = t.x; v[1] = t.y;
-    }
-}
-
-template <int VW> __device__ __forceinline__ void ldv(const __half *p, float (&v)[VW])
-{
-    if constexpr (VW == 1) {
-        v[0] = __half2float(__ldg(p));
-    } else if constexpr (VW == 4) {
-        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    } else {
-        const unsigned t = __ldg(reinterpret_cast<const unsigned *>(p));
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t));
-        v[0] = a.x; v[1] = a.y;
-    }
-}
-
-template <int VW> __device__ __forceinline__ void stv(float *p, const float (&v)[VW])
-{
-    if constexpr (VW == 1) *p = v[0];
-    else if constexpr (VW == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-}
-
-template <int VW> __device__ __forceinline__ void stv(__half *p, const float (&v)[VW])
-{
-    if constexpr (VW == 1) {
-        *p = __float2half_rn(v[0]);
-    } else if constexpr (VW == 4) {
-        __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-        uint2 t;
-        t.x = *reinterpret_cast<unsigned *>(&a);
-        t.y = *reinterpret_cast<unsigned *>(&b);
-        *reinterpret_cast<uint2 *>(p) = t;
-    } else {
-        __half2 a = __floats2half2_rn(v[0], v[1]);
-        *reinterpret_cast<__half2 *>(p) = a;
-    }
-}
-
-// VW link words of a group.
-template <int VW, typename LinkT>
-__device__ __forceinline__ void ld_links(const LinkT *p, uint32_t (&L)[VW])
-{
-    if constexpr (VW == 1) {
-        L[0] = __ldg(p);
-    } else if constexpr (sizeof(LinkT) == 2 && VW == 4) {
-        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-        L[0] = t.x & 0xffffu; L[1] = t.x >> 16; L[2] = t.y & 0xffffu; L[3] = t.y >> 16;
-    } else if constexpr (sizeof(LinkT) == 2 && VW == 2) {
-        const unsigned t = __ldg(reinterpret_cast<const unsigned *>(p));
-        L[0] = t & 0xffffu; L[1] = t >> 16;
-    } else if constexpr (VW == 4) {
-        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
-        L[0] = t.x; L[1] = t.y; L[2] = t.z; L[3] = t.w;
-    } else {
-        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-        L[0] = t.x; L[1] = t.y;
-    }
-}
-
-// Store a group: one vector store when all VW nodes are lattice nodes, else node by node (the
-// tail of a row whose length is not a multiple of VW; the ghost after it must survive).
-template <int VW, typename T>
-__device__ __forceinline__ void st_group(T *p, const float (&v)[VW], bool full, int nvalid)
-{
-    if (full) {
-        stv<VW>(p, v);
-    } else {
-#pragma unroll
-        for (int j = 0; j < VW; ++j)
-            if (j < nvalid) st(p + j, v[j]);
-    }
-}
-
-// Gather, for direction (cx, cy, cz), the VW populations pulled from the row-shifted group at
-// p_row (same x0): x-shifts come from the neighbouring lane or a scalar load at a warp/row edge.
-template <int VW, typename ST>
-__device__ __forceinline__ void gather(const ST *p_row, int cx, bool own_left, bool own_right,
-                                       float (&src)[VW])
-{
-    float V[VW];
-    ldv<VW>(p_row, V);
-    if (cx == 0) {
-#pragma unroll
-        for (int j = 0; j < VW; ++j) src[j] = V[j];
-    } else if (cx > 0) {
-        float left = __shfl_up_sync(0xffffffffu, V[VW - 1], 1);
-        if (own_left) left = ld(p_row - 1);
-        src[0] = left;
-#pragma unroll
-        for (int j = 1; j < VW; ++j) src[j] = V[j - 1];
-    } else {
-        float right = __shfl_down_sync(0xffffffffu, V[0], 1);
-        if (own_right) right = ld(p_row + VW);
-#pragma unroll
-        for (int j = 0; j < VW - 1; ++j) src[j] = V[j + 1];
-        src[VW - 1] = right;
-    }
-}
-
-// The node group's own populations of the opposite plane, for bounce-back along bit `bit`.
-template <int VW, int BB, typename ST>
-__device__ __forceinline__ void own_opposite(const ST *p, const uint32_t (&L)[VW], int bit,
-                                             float (&own)[VW])
-{
-    if (BB == 0) {
-        ldv<VW>(p, own);
-    } else {
-        uint32_t any = 0;
-#pragma unroll
-        for (int j = 0; j < VW; ++j) any |= (L[j] >> bit) & 1u;
-        if (any) {
-            ldv<VW>(p, own);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VW; ++j) own[j] = 0.f;
-        }
-    }
-}
+// A plain (coherent) load, for values this thread stored earlier in the same kernel.
+__device__ __forceinline__ float ldplain(const float *p) { return *p; }
+__device__ __forceinline__ float ldplain(const __half *p) { return __half2float(*p); }
 
 template <typename T> __device__ __forceinline__ T warp_sum(T v)
 {
@@ -305,26 +174,29 @@ __device__ __forceinline__ void ghost_images(const Geo &g, const int (&bc)[3], S
             }
 }
 
-// Flow ghost writes of node p with post-collision deviations d[i] and velocity u.
+// Flow ghost writes of node p (stored at k) with velocity (u0, u1, u2) and link word L; the
+// node's post-collision populations are read back from pop, where this thread just stored them.
 template <int DIM, typename ST>
-__device__ void flow_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
-                            const float *d, const float *u)
+__device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+                                         long long k, uint32_t L, float u0, float u1, float u2)
 {
     using F = FlowSet<DIM>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
     const int n[3] = {a.geo.nx, a.geo.ny, a.geo.nz};
     const bool inout = a.bc[FA] == BC_INOUT;
-    const float uv[3] = {u[0], u[1], DIM == 3 ? u[2] : 0.f};
+    const float uv[3] = {u0, u1, DIM == 3 ? u2 : 0.f};
     const float uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
-#pragma unroll 1
+#pragma unroll
     for (int i = 1; i < F::Q; ++i) {
-        ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, d[i]);
+        const float di = ldplain(pop + (long long)i * a.geo.plane + k);
+        ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, di);
         if (!inout) continue;
         const int cf = F::c(i, FA);
-        if (p[FA] == 0 && cf == 1) {  // inlet: the node's own next-step pull along c_i
+        if (p[FA] == 0 && cf == 1 && !((L >> i) & 1u)) {  // inlet: the node's own next-step pull
             const int q0 = x - F::c(i, 0), q1 = y - F::c(i, 1), q2 = z - F::c(i, 2);
-            st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2), d[F::opp(i)] + a.bb_in[i]);
+            st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2),
+               ldplain(pop + (long long)F::opp(i) * a.geo.plane + k) + a.bb_in[i]);
         }
         if (p[FA] == n[FA] - 1 && cf == -1) {  // outlet ghost fed by this last-layer node
             const float cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
@@ -337,21 +209,24 @@ __device__ void flow_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, i
     }
 }
 
-// Transport ghost writes of node p with post-collision populations e[i].
+// Transport ghost writes of node p (stored at k) with link word L; the node's post-collision
+// populations are read back from pop.
 template <int DIM, typename ST>
-__device__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z, const float *e)
+__device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+                                        long long k, uint32_t L)
 {
     using A = AdeSet<DIM>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
     const int n[3] = {a.geo.nx, a.geo.ny, a.geo.nz};
     const bool inout = a.bc[FA] == BC_INOUT;
-#pragma unroll 1
+#pragma unroll
     for (int i = 1; i < A::Q; ++i) {
-        ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, e[i]);
+        const float ei = ldplain(pop + (long long)i * a.geo.plane + k);
+        ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei);
         if (!inout) continue;
         const int cf = A::c(i, FA);
-        if (p[FA] == 0 && cf == 1) {
+        if (p[FA] == 0 && cf == 1 && !((L >> (Links<DIM>::ADE_SELF + i)) & 1u)) {
             const int q0 = x - A::c(i, 0), q1 = y - A::c(i, 1), q2 = z - A::c(i, 2);
             st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2), a.gin_dev[i]);
         }
@@ -359,247 +234,160 @@ __device__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, in
             int b[3] = {x, y, z};
             b[FA] = n[FA];
             ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, b[0], b[1], b[2], true,
-                                     a.ade_dirichlet ? a.gout_dev[i] : e[i]);
+                                     a.ade_dirichlet ? a.gout_dev[i] : ei);
         }
     }
 }
 
 // ---- the step kernel -------------------------------------------------------------------------
 
-// Launch variants (chosen per lattice, the results are identical bit for bit):
-//   VW  nodes per thread (1, 2 or 4);
-//   BB  0: the own opposite populations are loaded for every direction, independent of the link
-//       word (no load waits on another); 1: only when a node of the group bounces back.
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int VW, int BB>
-__global__ void __launch_bounds__(256) lbm_step_kernel(const StepArgs<DIM, ST> a)
+template <int DIM>
+__device__ __forceinline__ bool block_on_open_boundary(const Geo &g, const int (&bc)[3])
+{
+    bool b = bc[0] != BC_WALL && (blockIdx.x == 0 || (blockIdx.x + 1) * blockDim.x >= (unsigned)g.nx);
+    b = b || (bc[1] != BC_WALL && (blockIdx.y == 0 || blockIdx.y == (unsigned)g.ny - 1));
+    if (DIM == 3) b = b || (bc[2] != BC_WALL && (blockIdx.z == 0 || blockIdx.z == (unsigned)g.nz - 1));
+    return b;
+}
+
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
+__global__ void __launch_bounds__(256, DIM == 2 ? 8 : 1) lbm_step_kernel(const StepArgs<DIM, ST> a)
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM>;
     using LK = Links<DIM>;
-    const Geo &g = a.geo;
-    const int lane = threadIdx.x & 31;
+    const Geo g = a.geo;
     double acc[NSUM];
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
 
-    {
-        const int gx = blockIdx.x * blockDim.x + threadIdx.x;
-        const int y = blockIdx.y, z = blockIdx.z;
-        const bool live = gx < a.gpr;
-        // lanes past the end of the row repeat the last group, which keeps the shuffles defined
-        const int x0 = VW * (live ? gx : a.gpr - 1);
-        const long long k0 = g.at(x0, y, z);
-        const int nvalid = live ? min(VW, g.nx - x0) : 0;
-        const bool full = nvalid == VW;
-        const bool own_left = lane == 0 || x0 == 0;
-        const bool own_right = lane == 31 || x0 + VW >= VW * a.gpr;
-        uint32_t L[VW];
-        ld_links<VW>(a.link + k0, L);
-        bool ghosts = false;
-#pragma unroll
-        for (int j = 0; j < VW; ++j)
-            ghosts = ghosts || (j < nvalid && on_open_boundary<DIM>(g, a.bc, x0 + j, y, z));
-        float u[VW][3];
-#pragma unroll
-        for (int j = 0; j < VW; ++j) u[j][0] = u[j][1] = u[j][2] = 0.f;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    // threads past the end of the row: nothing to do, except join the block reduction of a
+    // check step (they compute on a copy of the last node and store nothing)
+    if (MODE != MODE_CHECK && x >= g.nx) return;
+    const bool valid = MODE != MODE_CHECK || x < g.nx;
+    const long long k = g.at(x < g.nx ? x : g.nx - 1, y, z);
+    const uint32_t L = __ldg(a.link + k);
+    const bool ghosts = block_on_open_boundary<DIM>(g, a.bc) && valid && on_open_boundary<DIM>(g, a.bc, x, y, z);
+    float u[3] = {0.f, 0.f, 0.f};
 
-        if (FLOW) {
-            float d[F::Q][VW];
-            ldv<VW>(a.fsrc + k0, d[0]);
+    if (FLOW) {
+        float d[F::Q];
 #pragma unroll
-            for (int i = 1; i < F::Q; ++i) {
-                const long long ks = k0 - ((long long)F::c(i, 1) * g.px + (long long)F::c(i, 2) * g.zs);
-                float src[VW], own[VW];
-                gather<VW>(a.fsrc + (long long)i * g.plane + ks, F::c(i, 0), own_left, own_right, src);
-                own_opposite<VW, BB>(a.fsrc + (long long)F::opp(i) * g.plane + k0, L, i, own);
-#pragma unroll
-                for (int j = 0; j < VW; ++j) d[i][j] = ((L[j] >> i) & 1u) ? own[j] : src[j];
-            }
-            float rp[VW], moved[VW];
-#pragma unroll
-            for (int j = 0; j < VW; ++j) {
-                const bool open = !(L[j] & (1u << LK::FLOW_SELF));
-                float r0 = 0.f, jx[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < F::Q; ++i) {
-                    if (!open) d[i][j] = 0.f;  // blocked nodes hold no populations
-                    r0 += d[i][j];
-#pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) jx[ax] += F::c(i, ax) * d[i][j];
-                }
-                rp[j] = r0;
-                const float inv = 1.0f / (1.0f + r0);
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) u[j][ax] = jx[ax] * inv;
-                moved[j] = 0.f;
-            }
-            // BGK relaxation of the moving populations, then the rest one closes the mass.
-#pragma unroll
-            for (int i = 1; i < F::Q; ++i) {
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    float cu = 0.f, uu = 0.f;
-#pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) {
-                        cu += F::c(i, ax) * u[j][ax];
-                        uu += u[j][ax] * u[j][ax];
-                    }
-                    const float feq = F::w(i) * (rp[j] + (1.0f + rp[j]) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-                    v[j] = kept(a.fdst, d[i][j] + a.omega * (feq - d[i][j]));
-                    d[i][j] = v[j];
-                    moved[j] += v[j];
-                }
-                st_group<VW>(a.fdst + (long long)i * g.plane + k0, v, full, nvalid);
-            }
-            {
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    v[j] = rp[j] - moved[j];
-                    d[0][j] = v[j];
-                }
-                st_group<VW>(a.fdst + k0, v, full, nvalid);
-            }
-            if (ghosts) {
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    if (j >= nvalid || (L[j] & (1u << LK::FLOW_SELF))) continue;
-                    if (!on_open_boundary<DIM>(g, a.bc, x0 + j, y, z)) continue;
-                    float dd[F::Q];
-#pragma unroll
-                    for (int i = 0; i < F::Q; ++i) dd[i] = d[i][j];
-                    flow_ghosts<DIM, ST>(a, a.fdst, x0 + j, y, z, dd, u[j]);
-                }
-            }
-            if (MODE != MODE_PLAIN) {
-                if (MODE == MODE_CHECK) {
-#pragma unroll
-                    for (int j = 0; j < VW; ++j) {
-                        if (j >= nvalid || (L[j] & (1u << LK::FLOW_SELF))) continue;
-                        double du2 = 0.0, u2 = 0.0;
-#pragma unroll
-                        for (int ax = 0; ax < DIM; ++ax) {
-                            const double un = u[j][ax];
-                            const double dd = un - (double)a.fld_u[ax * g.plane + k0 + j];
-                            du2 += dd * dd;
-                            u2 += un * un;
-                        }
-                        acc[SUM_DU2] += du2;
-                        acc[SUM_U2] += u2;
-                        acc[SUM_MASS] += 1.0 + (double)rp[j];
-                        if (!isfinite(rp[j]) || !isfinite(u2)) acc[SUM_BAD] += 1.0;
-                    }
-                }
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) v[j] = (L[j] & (1u << LK::FLOW_SELF)) ? 0.f : rp[j];
-                st_group<VW>(a.fld_rho + k0, v, full, nvalid);
-#pragma unroll
-                for (int ax = 0; ax < DIM; ++ax) {
-#pragma unroll
-                    for (int j = 0; j < VW; ++j) v[j] = u[j][ax];
-                    st_group<VW>(a.fld_u + ax * g.plane + k0, v, full, nvalid);
-                }
+        for (int i = 0; i < F::Q; ++i) {
+            const long long off = F::c(i, 0) + (long long)F::c(i, 1) * g.px + (long long)F::c(i, 2) * g.zs;
+            const float src = ld(a.fsrc + (long long)i * g.plane + k - off);
+            if (i == 0) {
+                d[0] = src;
+            } else {
+                const float own = ld(a.fsrc + (long long)F::opp(i) * g.plane + k);
+                d[i] = ((L >> i) & 1u) ? own : src;
             }
         }
-
-        if (ADE) {
-            if (FLOW) {
+        const bool open = !(L & (1u << LK::FLOW_SELF));
+        float rp = 0.f, j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int j = 0; j < VW; ++j) {
+        for (int i = 0; i < F::Q; ++i) {
+            if (!open) d[i] = 0.f;  // blocked nodes hold no populations
+            rp += d[i];
 #pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) u[j][ax] *= a.u_scale;  // 0 on flow-blocked nodes
-                }
-            } else {
+            for (int ax = 0; ax < DIM; ++ax) j[ax] += F::c(i, ax) * d[i];
+        }
+        const float inv = __fdividef(1.0f, 1.0f + rp);  // fast reciprocal, <= 2 ulp
+        float uu = 0.f;
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) {
+            u[ax] = j[ax] * inv;
+            uu += u[ax] * u[ax];
+        }
+        // BGK relaxation of the moving populations, then the rest one closes the mass
+        float moved = 0.f;
+#pragma unroll
+        for (int i = 1; i < F::Q; ++i) {
+            float cu = 0.f;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) cu += F::c(i, ax) * u[ax];
+            const float feq = F::w(i) * (rp + (1.0f + rp) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
+            moved += v;
+            if (valid) st(a.fdst + (long long)i * g.plane + k, v);
+        }
+        if (valid) st(a.fdst + k, rp - moved);
+        if (ghosts && open) flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, k, L, u[0], u[1], u[2]);
+        if (MODE != MODE_PLAIN && valid) {
+            if (MODE == MODE_CHECK && open) {
+                double du2 = 0.0, u2 = 0.0;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) {
-                    float v[VW];
-                    ldv<VW>(a.fld_u + ax * g.plane + k0, v);
-#pragma unroll
-                    for (int j = 0; j < VW; ++j)
-                        u[j][ax] = (L[j] & (1u << LK::FLOW_SELF)) ? 0.f : v[j] * a.u_scale;
+                    const double un = u[ax];
+                    const double dd = un - (double)a.fld_u[ax * g.plane + k];
+                    du2 += dd * dd;
+                    u2 += un * un;
                 }
+                acc[SUM_DU2] += du2;
+                acc[SUM_U2] += u2;
+                acc[SUM_MASS] += 1.0 + (double)rp;
+                if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] += 1.0;
             }
-            float e[A::Q][VW];
-            ldv<VW>(a.gsrc + k0, e[0]);
+            a.fld_rho[k] = rp;
 #pragma unroll
-            for (int i = 1; i < A::Q; ++i) {
-                const long long ks = k0 - ((long long)A::c(i, 1) * g.px + (long long)A::c(i, 2) * g.zs);
-                float src[VW], own[VW];
-                gather<VW>(a.gsrc + (long long)i * g.plane + ks, A::c(i, 0), own_left, own_right, src);
-                own_opposite<VW, BB>(a.gsrc + (long long)A::opp(i) * g.plane + k0, L, LK::ADE_SELF + i, own);
+            for (int ax = 0; ax < DIM; ++ax) a.fld_u[ax * g.plane + k] = u[ax];
+        }
+    }
+
+    if (ADE) {
+        if (FLOW) {
 #pragma unroll
-                for (int j = 0; j < VW; ++j) e[i][j] = ((L[j] >> (LK::ADE_SELF + i)) & 1u) ? own[j] : src[j];
+            for (int ax = 0; ax < DIM; ++ax) u[ax] *= a.u_scale;  // 0 on flow-blocked nodes
+        } else if (!(L & (1u << LK::FLOW_SELF))) {
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) u[ax] = a.fld_u[ax * g.plane + k] * a.u_scale;
+        }
+        float e[A::Q];
+#pragma unroll
+        for (int i = 0; i < A::Q; ++i) {
+            const long long off = A::c(i, 0) + (long long)A::c(i, 1) * g.px + (long long)A::c(i, 2) * g.zs;
+            const float src = ld(a.gsrc + (long long)i * g.plane + k - off);
+            if (i == 0) {
+                e[0] = src;
+            } else {
+                const float own = ld(a.gsrc + (long long)A::opp(i) * g.plane + k);
+                e[i] = ((L >> (LK::ADE_SELF + i)) & 1u) ? own : src;
             }
-            float cp[VW], sink[VW], moved[VW];
+        }
+        const bool open = !(L & (1u << LK::ADE_SELF));
+        float cp = 0.f;
 #pragma unroll
-            for (int j = 0; j < VW; ++j) {
-                const bool open = !(L[j] & (1u << LK::ADE_SELF));
-                float c0 = 0.f;
+        for (int i = 0; i < A::Q; ++i) {
+            if (!open) e[i] = 0.f;
+            cp += e[i];
+        }
+        const float sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : 0.0f;
+        float moved = 0.f;
 #pragma unroll
-                for (int i = 0; i < A::Q; ++i) {
-                    if (!open) e[i][j] = 0.f;
-                    c0 += e[i][j];
-                }
-                cp[j] = c0;
-                sink[j] = (L[j] & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + c0) : 0.0f;
-                moved[j] = 0.f;
+        for (int i = 1; i < A::Q; ++i) {
+            float cu = 0.f;
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) cu += A::c(i, ax) * u[ax];
+            const float geq = A::w(i) * (cp + (a.c_ref + cp) * cu * A::inv_cs2);
+            const float v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - A::w(i) * sink);
+            moved += v;
+            if (valid) st(a.gdst + (long long)i * g.plane + k, v);
+        }
+        if (valid) st(a.gdst + k, cp - sink - moved);
+        if (ghosts && open) ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, k, L);
+        if (MODE != MODE_PLAIN && valid) {
+            if (MODE == MODE_CHECK && open) {
+                const double Cn = (double)a.c_ref + (double)cp;
+                const double dc = (double)cp - (double)a.fld_c[k];
+                acc[SUM_DC2] += dc * dc;
+                acc[SUM_C2] += Cn * Cn;
+                acc[SUM_C] += Cn;
+                if (L & (1u << LK::SINK)) acc[SUM_CURRENT] += (double)a.k_sink * Cn;
+                if (!isfinite(cp)) acc[SUM_BAD] += 1.0;
             }
-#pragma unroll
-            for (int i = 1; i < A::Q; ++i) {
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    float cu = 0.f;
-#pragma unroll
-                    for (int ax = 0; ax < DIM; ++ax) cu += A::c(i, ax) * u[j][ax];
-                    const float geq = A::w(i) * (cp[j] + (a.c_ref + cp[j]) * cu * A::inv_cs2);
-                    v[j] = kept(a.gdst, e[i][j] + a.omega_c * (geq - e[i][j]) - A::w(i) * sink[j]);
-                    e[i][j] = v[j];
-                    moved[j] += v[j];
-                }
-                st_group<VW>(a.gdst + (long long)i * g.plane + k0, v, full, nvalid);
-            }
-            {
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    v[j] = cp[j] - sink[j] - moved[j];
-                    e[0][j] = v[j];
-                }
-                st_group<VW>(a.gdst + k0, v, full, nvalid);
-            }
-            if (ghosts) {
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    if (j >= nvalid || (L[j] & (1u << LK::ADE_SELF))) continue;
-                    if (!on_open_boundary<DIM>(g, a.bc, x0 + j, y, z)) continue;
-                    float ee[A::Q];
-#pragma unroll
-                    for (int i = 0; i < A::Q; ++i) ee[i] = e[i][j];
-                    ade_ghosts<DIM, ST>(a, a.gdst, x0 + j, y, z, ee);
-                }
-            }
-            if (MODE != MODE_PLAIN) {
-                if (MODE == MODE_CHECK) {
-#pragma unroll
-                    for (int j = 0; j < VW; ++j) {
-                        if (j >= nvalid || (L[j] & (1u << LK::ADE_SELF))) continue;
-                        const double Cn = (double)a.c_ref + (double)cp[j];
-                        const double dc = (double)cp[j] - (double)a.fld_c[k0 + j];
-                        acc[SUM_DC2] += dc * dc;
-                        acc[SUM_C2] += Cn * Cn;
-                        acc[SUM_C] += Cn;
-                        if (L[j] & (1u << LK::SINK)) acc[SUM_CURRENT] += (double)a.k_sink * Cn;
-                        if (!isfinite(cp[j])) acc[SUM_BAD] += 1.0;
-                    }
-                }
-                float v[VW];
-#pragma unroll
-                for (int j = 0; j < VW; ++j) v[j] = (L[j] & (1u << LK::ADE_SELF)) ? -a.c_ref : cp[j];
-                st_group<VW>(a.fld_c + k0, v, full, nvalid);
-            }
+            a.fld_c[k] = open ? cp : -a.c_ref;
         }
     }
     if (MODE == MODE_CHECK) block_partials(acc, a.partials);
@@ -618,11 +406,11 @@ __global__ void fill_ghosts_kernel(const StepArgs<DIM, ST> a)
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(q % g.nx), y = (int)((q / g.nx) % g.ny), z = (int)(q / ((long long)g.nx * g.ny));
-        if (!on_open_boundary<DIM>(g, a.bc, x, y, z)) continue;
         const long long k = g.at(x, y, z);
         const uint32_t L = a.link[k];
         if (!(L & (1u << LK::FLOW_SELF))) {
             float d[F::Q], rp = 0.f, j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
             for (int i = 0; i < F::Q; ++i) {
                 d[i] = ld(a.fdst + (long long)i * g.plane + k);
                 rp += d[i];
@@ -630,12 +418,12 @@ __global__ void fill_ghosts_kernel(const StepArgs<DIM, ST> a)
             }
             float u[3] = {0.f, 0.f, 0.f};
             for (int ax = 0; ax < DIM; ++ax) u[ax] = j[ax] / (1.0f + rp);
-            flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, d, u);
+            if (on_open_boundary<DIM>(g, a.bc, x, y, z)) flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, k, L, u[0], u[1], u[2]);
         }
         if (!(L & (1u << LK::ADE_SELF))) {
             float e[A::Q];
             for (int i = 0; i < A::Q; ++i) e[i] = ld(a.gdst + (long long)i * g.plane + k);
-            ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, e);
+            if (on_open_boundary<DIM>(g, a.bc, x, y, z)) ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, k, L);
         }
     }
 }

@@ -10,10 +10,8 @@ namespace mfc {
 
 enum : int { KIND_COUPLED = 0, KIND_FLOW = 1, KIND_ADE = 2 };
 
-// Default launch variant of the step kernels: nodes per thread (4 in 2-D: 128-bit FP32
-// accesses; 2 in 3-D), own-opposite load mode, threads per block.
-inline int default_vw(int dim) { return dim == 2 ? 4 : 2; }
-enum : int { DEFAULT_BB = 0, DEFAULT_BLOCK = 256 };
+// Default threads per block of the step kernels.
+enum : int { DEFAULT_BLOCK = 128 };
 
 // Everything a step launch needs, independent of dimension and storage type.
 struct StepHost {
@@ -21,13 +19,8 @@ struct StepHost {
     int kind, mode;
     Geo geo;
     int bc[3];
-    int vw, bb;       // launch variant: nodes per thread, own-opposite load mode
-    int staged;       // 1: TMA-staged kernel (2-D), block threads = strip width
-    int *err;         // pipeline error flag (staged kernel)
     int nblocks;      // out: blocks of the launch (one reduction partial each)
-    int gpr;
-    long long ngroups;
-    int grid, block;
+    int grid, block;  // grid.x (blocks along a row) and threads per block
     const void *fsrc;
     void *fdst;
     const void *gsrc;
@@ -49,11 +42,6 @@ cudaError_t launch_fill_ghosts_2d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_2d_f16(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f16(const StepHost &h, cudaStream_t s);
-
-// Staged-kernel plan: strips of h.block columns, segments of seg_rows rows, sized from the
-// occupancy of the kernel so that one wave covers the lattice.
-void staged_plan_2d_f32(const StepHost &h, int *nstrips, int *seg_rows);
-void staged_plan_2d_f16(const StepHost &h, int *nstrips, int *seg_rows);
 
 inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
 {

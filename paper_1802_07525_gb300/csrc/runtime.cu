@@ -103,10 +103,8 @@ struct mfc_lattice {
     cudaEvent_t done = nullptr;
     float c_ref = 1.0f;
     int grid = 1, block = DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
-    int vw = 4, bb = DEFAULT_BB, staged = 0;
-    int *err_d = nullptr;  // pipeline error flag, lives after the results
-    int gpr = 1;
-    long long ngroups = 1;
+
+
     std::vector<GraphEntry> graphs;
     long flow_open = 0, ade_open = 0;
     double last_current = 0.0;
@@ -219,33 +217,27 @@ Layout layout_of(const mfc_lattice_desc *d)
     g.nx = d->nx;
     g.ny = d->ny;
     g.nz = d->dim == 2 ? 1 : d->nz;
-    // pitch and front offset are multiples of 8 elements, so that 16-byte bulk copies of
-    // FP16 rows (and of 16-bit link rows) start aligned
+    // pitch and front offset are multiples of 8 elements (32-byte aligned FP32 rows)
     g.px = (int)round_up((size_t)g.nx + 2, 8);
     g.zs = (long long)(g.ny + 2) * g.px;
     const int gz = d->dim == 3 ? 1 : 0;
     g.row0 = 8 + ((long long)gz * (g.ny + 2) + 1) * g.px;
     const long long last = g.at(0, g.ny + 1, g.nz - 1 + gz);  // first element past the last ghost row
-    // slack for the widest staged copy of the last ghost row (a strip of up to 256 + halo)
-    g.plane = (long long)round_up((size_t)(last + 2 * g.px + 512 + 64), 64);
+    g.plane = (long long)round_up((size_t)(last + 2 * g.px + 64), 64);
     l.N = (long long)g.nx * g.ny * g.nz;
     l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
     l.link_bytes = d->dim == 2 ? 2 : 4;
     return l;
 }
 
-// Launch shape of a variant: one thread per group of vw nodes of a row, grid (groups of a row /
-// block, ny, nz).
+// Launch shape: one thread per node, grid (row / block, ny, nz).
 void choose_launch(mfc_lattice *L)
 {
-    L->gpr = (L->nx + L->vw - 1) / L->vw;
-    L->ngroups = (long long)L->gpr * L->ny * L->nz;
-    L->grid = (L->gpr + L->block - 1) / L->block;
+    L->grid = (L->nx + L->block - 1) / L->block;
     L->nblocks = L->grid * L->ny * L->nz;
 }
 
-// Blocks of the largest launch any variant makes (one node per thread, 128 threads per block):
-// the size of the partial-sum buffer.
+// Blocks of the largest launch (128 threads per block): the size of the partial-sum buffer.
 int max_launch_blocks(const Layout &l)
 {
     return (l.geo.nx + 127) / 128 * l.geo.ny * l.geo.nz;
@@ -260,12 +252,7 @@ void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->mode = mode;
     h->geo = L->geo;
     for (int a = 0; a < 3; ++a) h->bc[a] = a < L->dim ? L->desc.bc[a] : MFC_BC_PERIODIC;
-    h->vw = L->vw;
-    h->bb = L->bb;
-    h->staged = L->staged;
-    h->err = L->err_d;
-    h->gpr = L->gpr;
-    h->ngroups = L->ngroups;
+
     h->grid = L->grid;
     h->block = L->block;
     h->fsrc = L->f[L->fcur];
@@ -337,8 +324,7 @@ mfc_status enqueue_block(mfc_lattice *L, int kind, int n, bool check)
     }
     if (check) {
         CK(L, launch_finalize(L->partials, nb, L->results_d, L->stream));
-        // the results and, after them, the pipeline error flag
-        CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * (NRESULT + 1),
+        CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * NRESULT,
                               cudaMemcpyDeviceToHost, L->stream));
     }
     return MFC_OK;
@@ -435,8 +421,6 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
         *steps += n;
         if (n >= 2) {
             const double *r = L->results_h;
-            if (*reinterpret_cast<const int *>(r + NRESULT) != 0)
-                return fail(L, MFC_ERR_CUDA, "a staged copy did not complete within the wait limit");
             if (kind != KIND_ADE) *res_f = r[RES_FLOW];
             if (kind != KIND_FLOW) {
                 *res_a = r[RES_ADE];
@@ -584,8 +568,6 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     // transport storage offset: 0, so that the no-substrate start state is stored exactly
     L->c_ref = 0.0f;
     cudaGetDevice(&L->device);
-    L->vw = default_vw(L->dim);
-    L->bb = DEFAULT_BB;
     L->block = DEFAULT_BLOCK;
     L->max_blocks = max_launch_blocks(l);
     choose_launch(L);
@@ -615,15 +597,14 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
     ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
     ok = ok && dalloc((void **)&L->partials, (size_t)L->max_blocks * NSUM * sizeof(double));
-    ok = ok && dalloc((void **)&L->results_d, (NRESULT + 1) * sizeof(double));
+    ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
     ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
     if (!ok) {
         release(L);
         delete L;
         return fail(nullptr, MFC_ERR_OOM, "device allocation failed");
     }
-    L->err_d = reinterpret_cast<int *>(L->results_d + NRESULT);
-    cudaError_t e = cudaHostAlloc((void **)&L->results_h, (NRESULT + 1) * sizeof(double), cudaHostAllocDefault);
+    cudaError_t e = cudaHostAlloc((void **)&L->results_h, NRESULT * sizeof(double), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&L->counts_h, 2 * sizeof(unsigned long long), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
     if (e == cudaSuccess) {
@@ -640,7 +621,7 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
         delete L;
         return fail(nullptr, MFC_ERR_CUDA, msg);
     }
-    memset(L->results_h, 0, (NRESULT + 1) * sizeof(double));
+    memset(L->results_h, 0, NRESULT * sizeof(double));
     // every node open, rest state
     e = cudaMemsetAsync(L->cls_cur, 0, round_up((size_t)l.N, 256), L->stream);
     if (e != cudaSuccess) {
@@ -883,18 +864,9 @@ MFC_API mfc_status mfc_set_launch(mfc_lattice *L, const mfc_launch *v)
     mfc_status st = enter(L);
     if (st != MFC_OK) return st;
     if (!v) return fail(L, MFC_ERR_ARG, "launch is NULL");
-    const bool vw_ok = v->nodes_per_thread == 1 || v->nodes_per_thread == 2 ||
-                       (v->nodes_per_thread == 4 && L->dim == 2);
-    const bool blk_ok = v->block == 128 || v->block == 256;
-    const bool st_ok = v->staged == 0 || (v->staged == 1 && L->dim == 2);
-    if (!vw_ok || !blk_ok || !st_ok || (v->bounce_loads != 0 && v->bounce_loads != 1))
-        return fail(L, MFC_ERR_ARG, "launch variant not available (nodes_per_thread 1|2|4 (4 in 2-D), "
-                                    "bounce_loads 0|1, block 128|256, staged 0|1 (1 in 2-D))");
+    if (v->block != 128 && v->block != 256) return fail(L, MFC_ERR_ARG, "block must be 128 or 256");
     CK(L, cudaStreamSynchronize(L->stream));
-    L->vw = v->nodes_per_thread;
-    L->bb = v->bounce_loads;
     L->block = v->block;
-    L->staged = v->staged;
     choose_launch(L);
     drop_graphs(L);
     return MFC_OK;
@@ -903,10 +875,7 @@ MFC_API mfc_status mfc_set_launch(mfc_lattice *L, const mfc_launch *v)
 MFC_API mfc_status mfc_get_launch(mfc_lattice *L, mfc_launch *v)
 {
     if (!L || !v) return MFC_ERR_ARG;
-    v->nodes_per_thread = L->vw;
-    v->bounce_loads = L->bb;
     v->block = L->block;
-    v->staged = L->staged;
     return MFC_OK;
 }
 

@@ -59,8 +59,7 @@ class SolveResult(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("nodes_per_thread", ctypes.c_int), ("bounce_loads", ctypes.c_int),
-                ("block", ctypes.c_int), ("staged", ctypes.c_int)]
+    _fields_ = [("block", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -260,8 +259,8 @@ class Lattice:
         v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(q, self.N))
         self._check(self._L.mfc_write_populations(self.handle, which, _ptr(v)))
 
-    def set_launch(self, nodes_per_thread=1, bounce_loads=0, block=256, staged=0):
-        v = Launch(int(nodes_per_thread), int(bounce_loads), int(block), int(staged))
+    def set_launch(self, block=128):
+        v = Launch(int(block))
         self._check(self._L.mfc_set_launch(self.handle, ctypes.byref(v)))
 
     def get_launch(self) -> dict:
