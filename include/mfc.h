@@ -188,6 +188,35 @@ typedef struct {
 MFC_API mfc_status mfc_set_launch(mfc_lattice *lat, const mfc_launch *launch);
 MFC_API mfc_status mfc_get_launch(mfc_lattice *lat, mfc_launch *launch);
 
+/* ---- sums without allocation ------------------------------------------------------------ */
+
+/* For callers that cannot allocate device memory (code inside another framework's memory pool
+ * or under a fixed device-memory budget, where a raw cudaMalloc would break the accounting or is
+ * not allowed, and paths that must not risk an allocation failure).  The paper has no
+ * counterpart: this is the check-step reduction of mfc_solve_steady (the eight FP64 sums and
+ * the two residuals) applied to fields the caller already holds in device memory.
+ *
+ * Inputs (device pointers, dense, x fastest): node_class[n] (bit 0 flow-blocked, bit 1
+ * transport-blocked, bit 2 consumption), rho[n], u[dim*n] and u_prev[dim*n] (component-major),
+ * c[n] and c_prev[n].  Output: out[10] in device memory, the sums sum |u-u_prev|^2, sum |u|^2,
+ * sum rho (flow-open nodes), sum (c-c_prev)^2, sum c^2, sum c (transport-open nodes), sum over
+ * consumption nodes of k_sink*c, the count of non-finite values, then the flow and transport
+ * residuals.  Queued on `stream` (cudaStream_t; NULL for the legacy default stream).
+ *
+ * It allocates nothing: its per-block partial sums live in a file-scope device array of 512 KiB
+ * (256 nodes per block, 8192 blocks) that every GPU which loads the library holds until the
+ * process exits, so n is limited to 2,097,152 nodes (MFC_ERR_ARG above that, or for dim not 2/3
+ * or a NULL pointer).  The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress); make that first call before any stream capture.  Every call on a GPU
+ * shares that GPU's array and it keeps the last call's partials: two calls whose kernels can
+ * run at the same time on one GPU (for instance on different streams) race on it, so order them
+ * (same stream, or an event between them).  Each call writes every partial it reads, so nothing
+ * needs clearing between calls. */
+MFC_API mfc_status mfc_field_sums_noalloc(long long n, int dim, const uint8_t *node_class,
+                                          const double *rho, const double *u, const double *u_prev,
+                                          const double *c, const double *c_prev, double k_sink,
+                                          double *out, void *stream);
+
 /* ---- introspection --------------------------------------------------------------------- */
 
 /* Number of nodes open for flow and for transport (computed at mfc_set_geometry). */

@@ -94,6 +94,8 @@ _SIGS = {
     "mfc_synchronize": (ctypes.c_int, [_vp]),
     "mfc_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
+    "mfc_field_sums_noalloc": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                              _vp, _vp, ctypes.c_double, _vp, _vp]),
     "mfc_active_nodes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_long),
                                         ctypes.POINTER(ctypes.c_long)]),
     "mfc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
