@@ -27,7 +27,8 @@
 // as g_i - w_i c_ref; FP32 or FP16 storage, FP32 arithmetic.  The rest population of each lattice
 // is written as the conserved total (rho - 1, or C - kC) minus the stored moving populations, so
 // rounding cannot drift mass or substrate.  Check steps accumulate residual, mass, substrate and
-// current sums in FP64 (warp shuffles, shared memory, one partial per block).
+// current sums: per node and over a warp in FP32, over warps, blocks and the lattice in FP64 (one
+// partial per block, added in a fixed order by a single-block kernel).
 #pragma once
 
 #include "lbm_lattice.cuh"
@@ -90,8 +91,11 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Sum NSUM doubles over the block; thread 0 writes them to partials[block].
-__device__ __forceinline__ void block_partials(double (&acc)[NSUM], double *partials)
+// Sum the NSUM per-node terms over the block; thread 0 writes them to partials[block].  A node's
+// terms and the sum over a warp (32 terms) are FP32; everything past the warp is FP64 (GB300's
+// FP64 rate is a small fraction of its FP32 rate, so per-node FP64 work would dominate the
+// check step).
+__device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *partials)
 {
     __shared__ double sh[32][NSUM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void block_partials(double (&acc)[NSUM], double *part
     for (int m = 0; m < NSUM; ++m) acc[m] = warp_sum(acc[m]);
     if (lane == 0) {
 #pragma unroll
-        for (int m = 0; m < NSUM; ++m) sh[warp][m] = acc[m];
+        for (int m = 0; m < NSUM; ++m) sh[warp][m] = (double)acc[m];
     }
     __syncthreads();
     if (warp == 0) {
@@ -251,15 +255,15 @@ __device__ __forceinline__ bool block_on_open_boundary(const Geo &g, const int (
 }
 
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
-__global__ void __launch_bounds__(256, DIM == 2 ? 8 : 1) lbm_step_kernel(const StepArgs<DIM, ST> a)
+__global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) : 1) lbm_step_kernel(const StepArgs<DIM, ST> a)
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM>;
     using LK = Links<DIM>;
     const Geo g = a.geo;
-    double acc[NSUM];
+    float acc[NSUM];
 #pragma unroll
-    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
+    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -317,18 +321,17 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 8 : 1) lbm_step_kernel(const S
         if (ghosts && open) flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, k, L, u[0], u[1], u[2]);
         if (MODE != MODE_PLAIN && valid) {
             if (MODE == MODE_CHECK && open) {
-                double du2 = 0.0, u2 = 0.0;
+                float du2 = 0.f, u2 = 0.f;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) {
-                    const double un = u[ax];
-                    const double dd = un - (double)a.fld_u[ax * g.plane + k];
+                    const float dd = u[ax] - a.fld_u[ax * g.plane + k];  // exact for nearby values
                     du2 += dd * dd;
-                    u2 += un * un;
+                    u2 += u[ax] * u[ax];
                 }
-                acc[SUM_DU2] += du2;
-                acc[SUM_U2] += u2;
-                acc[SUM_MASS] += 1.0 + (double)rp;
-                if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] += 1.0;
+                acc[SUM_DU2] = du2;
+                acc[SUM_U2] = u2;
+                acc[SUM_MASS] = 1.0f + rp;
+                if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] = 1.0f;
             }
             a.fld_rho[k] = rp;
 #pragma unroll
@@ -379,13 +382,13 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 8 : 1) lbm_step_kernel(const S
         if (ghosts && open) ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, k, L);
         if (MODE != MODE_PLAIN && valid) {
             if (MODE == MODE_CHECK && open) {
-                const double Cn = (double)a.c_ref + (double)cp;
-                const double dc = (double)cp - (double)a.fld_c[k];
-                acc[SUM_DC2] += dc * dc;
-                acc[SUM_C2] += Cn * Cn;
-                acc[SUM_C] += Cn;
-                if (L & (1u << LK::SINK)) acc[SUM_CURRENT] += (double)a.k_sink * Cn;
-                if (!isfinite(cp)) acc[SUM_BAD] += 1.0;
+                const float Cn = a.c_ref + cp;
+                const float dc = cp - a.fld_c[k];
+                acc[SUM_DC2] = dc * dc;
+                acc[SUM_C2] = Cn * Cn;
+                acc[SUM_C] = Cn;
+                if (L & (1u << LK::SINK)) acc[SUM_CURRENT] = a.k_sink * Cn;
+                if (!isfinite(cp)) acc[SUM_BAD] += 1.0f;
             }
             a.fld_c[k] = open ? cp : -a.c_ref;
         }
