@@ -142,7 +142,7 @@ def cpu_baseline(w, seconds_target=10.0):
 
 def traffic_record(kernel):
     """DRAM bytes per launch of the kernel from the committed ncu summary, if it was taken
-    on the library build that is loaded now (else None)."""
+    on the kernel code that is built now (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -150,7 +150,7 @@ def traffic_record(kernel):
         d = json.load(fh)
     from paper_1802_07525_gb300 import build
     rec = d.get(kernel)
-    if not rec or rec.get("build_digest") != build._digest(False):
+    if not rec or rec.get("kernel_digest") != build.kernel_digest(rec["translation_unit"]):
         return None
     return rec.get("dram_bytes_per_launch_full")
 

@@ -52,6 +52,21 @@ def _digest(verbose: bool) -> str:
     return h.hexdigest()
 
 
+# The files each step-kernel translation unit compiles from (the TU and the headers it includes).
+KERNEL_TU_FILES = ["lbm_launch.cuh", "mfc_internal.h", "lbm_kernels.cuh", "lbm_lattice.cuh"]
+
+
+def kernel_digest(tu: str) -> str:
+    """Digest of one step-kernel translation unit: its source, the headers it includes and the
+    flags.  A profile taken on a build with the same digest was taken on the same kernel code."""
+    h = hashlib.sha256()
+    for name in [tu] + KERNEL_TU_FILES:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(_flags(False)).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, quiet: bool = True) -> str:
     """Compile (if sources changed) and return the path of libmfc.so."""
     os.makedirs(OUT_DIR, exist_ok=True)

@@ -7,35 +7,55 @@
 
 namespace mfc {
 
-// Add the per-block partials in a fixed order; write the sums and the residuals.
-__global__ void __launch_bounds__(256) finalize_kernel(const double *partials, int nblocks,
-                                                        double *results)
+// Lattice sums in FP64, in a fixed order and in two stages spread over many SMs (a single block
+// would be bound by one SM's FP64 rate).  Stage 1: block b adds partials b, b + gridDim.x, ...
+// and writes one partial; stage 2: one block adds those and writes the sums and the residuals.
+__device__ __forceinline__ void block_sum_fp64(double (&acc)[NSUM], double *out)
 {
-    __shared__ double sh[256][NSUM];
+    __shared__ double sh[8][NSUM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) acc[m] = warp_sum(acc[m]);
+    if (lane == 0) {
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) sh[warp][m] = acc[m];
+    }
+    __syncthreads();
+    if (threadIdx.x < NSUM) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) finalize_stage1_kernel(const double *partials, int nblocks,
+                                                               double *stage1)
+{
     double acc[NSUM];
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    for (int b = blockIdx.x + gridDim.x * threadIdx.x; b < nblocks; b += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int m = 0; m < NSUM; ++m) acc[m] += partials[(size_t)b * NSUM + m];
     }
+    block_sum_fp64(acc, stage1 + (size_t)blockIdx.x * NSUM);
+}
+
+__global__ void __launch_bounds__(256) finalize_stage2_kernel(const double *stage1, int n1, double *results)
+{
+    double acc[NSUM];
 #pragma unroll
-    for (int m = 0; m < NSUM; ++m) sh[threadIdx.x][m] = acc[m];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
+    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
+    for (int b = threadIdx.x; b < n1; b += blockDim.x) {
 #pragma unroll
-            for (int m = 0; m < NSUM; ++m) sh[threadIdx.x][m] += sh[threadIdx.x + s][m];
-        }
-        __syncthreads();
+        for (int m = 0; m < NSUM; ++m) acc[m] += stage1[(size_t)b * NSUM + m];
     }
+    __shared__ double r[NSUM];
+    block_sum_fp64(acc, r);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double r[NSUM];
 #pragma unroll
-        for (int m = 0; m < NSUM; ++m) {
-            r[m] = sh[0][m];
-            results[m] = r[m];
-        }
+        for (int m = 0; m < NSUM; ++m) results[m] = r[m];
         results[RES_FLOW] = r[SUM_U2] > 0.0 ? sqrt(r[SUM_DU2] / r[SUM_U2])
                                             : (r[SUM_DU2] > 0.0 ? INFINITY : 0.0);
         results[RES_ADE] = r[SUM_C2] > 0.0 ? sqrt(r[SUM_DC2] / r[SUM_C2])

@@ -91,30 +91,27 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Sum the NSUM per-node terms over the block; thread 0 writes them to partials[block].  A node's
-// terms and the sum over a warp (32 terms) are FP32; everything past the warp is FP64 (GB300's
-// FP64 rate is a small fraction of its FP32 rate, so per-node FP64 work would dominate the
-// check step).
+// Sum the NSUM per-node terms over the block; thread 0 writes them, as doubles, to
+// partials[block].  Node terms and the sums over a warp and over the block (at most 256 terms)
+// are FP32; the sum over the blocks of the lattice is FP64 (finalize kernels).  GB300's FP64
+// rate is a small fraction of its FP32 rate, so per-warp FP64 work would dominate the check step.
 __device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *partials)
 {
-    __shared__ double sh[32][NSUM];
+    __shared__ float sh[8][NSUM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = warp_sum(acc[m]);
     if (lane == 0) {
 #pragma unroll
-        for (int m = 0; m < NSUM; ++m) sh[warp][m] = (double)acc[m];
+        for (int m = 0; m < NSUM; ++m) sh[warp][m] = acc[m];
     }
     __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int m = 0; m < NSUM; ++m) {
-            double v = lane < nwarp ? sh[lane][m] : 0.0;
-            v = warp_sum(v);
-            if (lane == 0)
-                partials[((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)) * NSUM + m] = v;
-        }
+    if (threadIdx.x < NSUM) {
+        float v = 0.f;
+        for (int w = 0; w < nwarp; ++w) v += sh[w][threadIdx.x];
+        partials[((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)) * NSUM +
+                 threadIdx.x] = (double)v;
     }
 }
 
@@ -275,6 +272,16 @@ __global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) :
     const uint32_t L = __ldg(a.link + k);
     const bool ghosts = block_on_open_boundary<DIM>(g, a.bc) && valid && on_open_boundary<DIM>(g, a.bc, x, y, z);
     float u[3] = {0.f, 0.f, 0.f};
+    // check step: the previous fields of this node (read before this thread overwrites them),
+    // issued first so that their latency overlaps the population loads
+    float u_prev[3] = {0.f, 0.f, 0.f}, c_prev = 0.f;
+    if (MODE == MODE_CHECK) {
+        if (FLOW) {
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) u_prev[ax] = ldplain(a.fld_u + ax * g.plane + k);
+        }
+        if (ADE) c_prev = ldplain(a.fld_c + k);
+    }
 
     if (FLOW) {
         float d[F::Q];
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) :
                 float du2 = 0.f, u2 = 0.f;
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) {
-                    const float dd = u[ax] - a.fld_u[ax * g.plane + k];  // exact for nearby values
+                    const float dd = u[ax] - u_prev[ax];  // exact for nearby values
                     du2 += dd * dd;
                     u2 += u[ax] * u[ax];
                 }
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) :
         if (MODE != MODE_PLAIN && valid) {
             if (MODE == MODE_CHECK && open) {
                 const float Cn = a.c_ref + cp;
-                const float dc = cp - a.fld_c[k];
+                const float dc = cp - c_prev;
                 acc[SUM_DC2] = dc * dc;
                 acc[SUM_C2] = Cn * Cn;
                 acc[SUM_C] = Cn;

@@ -56,7 +56,8 @@ inline cudaError_t launch_fill_ghosts(const StepHost &h, cudaStream_t s)
 }
 cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s);
 cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s);
-cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s);
+cudaError_t launch_finalize(const double *partials, int nblocks, double *stage1, double *results,
+                            cudaStream_t s);
 cudaError_t launch_fields_to_dense(const ConvArgs &a, cudaStream_t s);
 cudaError_t launch_pop_convert(const PopArgs &a, cudaStream_t s);
 

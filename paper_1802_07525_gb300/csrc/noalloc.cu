@@ -3,11 +3,11 @@
 //
 // Some callers cannot call cudaMalloc: code running inside another framework's memory pool or
 // under a fixed device-memory budget, where a raw allocation would break the accounting or is
-// forbidden, and code on a path that must not risk an allocation failure.  This entry point does
-// the work of the check-step reduction of mfc_solve_steady (the same FP64 sums, the same
-// per-block partials added in a fixed order) on fields the caller already holds, and allocates
-// nothing: its per-block partials live in the file-scope array below, which every GPU that
-// loads the library holds until the process exits.
+// forbidden, and code on a path that must not risk an allocation failure.  This entry point
+// computes the sums of the check step of mfc_solve_steady (per-block partials added in a fixed
+// order; here in FP64 throughout, on FP64 fields) on fields the caller already holds, and
+// allocates nothing: its per-block partials live in the file-scope array below, which every GPU
+// that loads the library holds until the process exits.
 #include <mutex>
 
 #include <cuda_runtime.h>

@@ -40,9 +40,17 @@ cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double *partials, int nblocks, double *results, cudaStream_t s)
+// Stage-1 blocks of the lattice sums (256 threads each, about 64 partials per block).
+constexpr int FINAL_STAGE1_MAX = 256;
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *stage1, double *results,
+                            cudaStream_t s)
 {
-    finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, results);
+    int n1 = (nblocks + 63) / 64;
+    if (n1 > FINAL_STAGE1_MAX) n1 = FINAL_STAGE1_MAX;
+    if (n1 < 1) n1 = 1;
+    finalize_stage1_kernel<<<n1, 256, 0, s>>>(partials, nblocks, stage1);
+    finalize_stage2_kernel<<<1, 256, 0, s>>>(stage1, n1, results);
     return cudaGetLastError();
 }
 
@@ -323,7 +331,8 @@ mfc_status enqueue_block(mfc_lattice *L, int kind, int n, bool check)
         if (st != MFC_OK) return st;
     }
     if (check) {
-        CK(L, launch_finalize(L->partials, nb, L->results_d, L->stream));
+        CK(L, launch_finalize(L->partials, nb, L->partials + (size_t)L->max_blocks * NSUM, L->results_d,
+                              L->stream));
         CK(L, cudaMemcpyAsync(L->results_h, L->results_d, sizeof(double) * NRESULT,
                               cudaMemcpyDeviceToHost, L->stream));
     }
@@ -528,7 +537,7 @@ MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
     b += (size_t)P * l.link_bytes;                // links
     b += 2 * round_up((size_t)l.N, 256);          // classes (current, next)
     b += (size_t)(2 + l.dim) * P * 4;             // fields
-    b += (size_t)max_launch_blocks(l) * NSUM * sizeof(double);  // partials
+    b += ((size_t)max_launch_blocks(l) + FINAL_STAGE1_MAX) * NSUM * sizeof(double);  // partials
     b += 4096;
     return b;
 }
@@ -596,7 +605,8 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
     ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
     ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
     ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
-    ok = ok && dalloc((void **)&L->partials, (size_t)L->max_blocks * NSUM * sizeof(double));
+    // per-block partials, then the stage-1 sums of the finalize
+    ok = ok && dalloc((void **)&L->partials, ((size_t)L->max_blocks + FINAL_STAGE1_MAX) * NSUM * sizeof(double));
     ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
     ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
     if (!ok) {
