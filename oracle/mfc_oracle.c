@@ -412,12 +412,16 @@ typedef struct {
 } orc_result;
 
 /* Iterate to equilibrium (method steps 2 and 3 of Sec. 3; "enough time steps until an
- * equilibrium is reached", Sec. 4).  The test is r = ||v^n - v^(n-1)|| / ||v^n|| < tol,
- * evaluated at steps n that are multiples of check_every (1 = every step).
+ * equilibrium is reached", Sec. 4, which fixes no criterion).  The test is the mean relative
+ * change per step since the previous check,
+ *     r = ||v^n - v^m|| / ((n - m) ||v^n||) < tol,
+ * evaluated at the check steps n: the multiples of check_every and the last step allowed;
+ * m is the previous check step, or the step of the fields given on entry (the last step run
+ * before the call).  With check_every = 1 it is the per-step change ||v^n - v^(n-1)|| / ||v^n||.
  * SEQUENTIAL: the flow runs to equilibrium, then transport runs with that velocity frozen
  * (the paper's order).  CONCURRENT: both advance together, transport using the same step's
  * flow velocity; both residuals must fall below their tolerances.
- * f, g: state in/out.  rho, u, conc: fields of the last step, out.  Returns converged. */
+ * f, g: state in/out.  rho, u, conc: fields of the last step, in/out.  Returns converged. */
 ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f, double *g,
                              double *rho, double *u, double *conc, int mode, double tol_flow,
                              double tol_ade, long max_steps, int check_every, orc_result *res)
@@ -427,55 +431,63 @@ ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f,
     int d = p->dim;
     double *f2 = calloc((size_t)vf.q * N, sizeof(double));
     double *g2 = calloc((size_t)va.q * N, sizeof(double));
-    double *u_prev = calloc((size_t)d * N, sizeof(double));
+    double *u_prev = calloc((size_t)d * N, sizeof(double));   /* fields at the previous check */
     double *c_prev = calloc((size_t)N, sizeof(double));
     double s[8];
     memset(res, 0, sizeof *res);
     int conv_f = 0, conv_a = 0;
     if (check_every < 1) check_every = 1;
+    memcpy(u_prev, u, sizeof(double) * d * N);
+    memcpy(c_prev, conc, sizeof(double) * N);
 
     if (mode == MODE_SEQUENTIAL) {
+        long m = 0;
         for (long n = 1; n <= max_steps; ++n) {
-            memcpy(u_prev, u, sizeof(double) * d * N);
             orc_flow_step(p, cls, f, f2, rho, u);
             memcpy(f, f2, sizeof(double) * vf.q * N);
             res->steps_flow = n;
-            if (n % check_every == 0) {
+            if (n % check_every == 0 || n == max_steps) {
                 orc_sums(p, cls, rho, u, u_prev, NULL, NULL, s);
-                res->res_flow = rel_residual(s[0], s[1]);
+                res->res_flow = rel_residual(s[0], s[1]) / (double)(n - m);
                 res->mass = s[2];
+                memcpy(u_prev, u, sizeof(double) * d * N);
+                m = n;
                 if (res->res_flow < tol_flow) { conv_f = 1; break; }
             }
         }
+        m = 0;
         for (long n = 1; n <= max_steps; ++n) {
-            memcpy(c_prev, conc, sizeof(double) * N);
             orc_ade_step(p, cls, g, g2, u, conc);
             memcpy(g, g2, sizeof(double) * va.q * N);
             res->steps_ade = n;
-            if (n % check_every == 0) {
+            if (n % check_every == 0 || n == max_steps) {
                 orc_sums(p, cls, NULL, u, u, conc, c_prev, s);
-                res->res_ade = rel_residual(s[3], s[4]);
+                res->res_ade = rel_residual(s[3], s[4]) / (double)(n - m);
                 res->substrate = s[5];
                 res->current = s[6];
+                memcpy(c_prev, conc, sizeof(double) * N);
+                m = n;
                 if (res->res_ade < tol_ade) { conv_a = 1; break; }
             }
         }
     } else {
+        long m = 0;
         for (long n = 1; n <= max_steps; ++n) {
-            memcpy(u_prev, u, sizeof(double) * d * N);
-            memcpy(c_prev, conc, sizeof(double) * N);
             orc_flow_step(p, cls, f, f2, rho, u);
             orc_ade_step(p, cls, g, g2, u, conc);
             memcpy(f, f2, sizeof(double) * vf.q * N);
             memcpy(g, g2, sizeof(double) * va.q * N);
             res->steps_flow = res->steps_ade = n;
-            if (n % check_every == 0) {
+            if (n % check_every == 0 || n == max_steps) {
                 orc_sums(p, cls, rho, u, u_prev, conc, c_prev, s);
-                res->res_flow = rel_residual(s[0], s[1]);
-                res->res_ade = rel_residual(s[3], s[4]);
+                res->res_flow = rel_residual(s[0], s[1]) / (double)(n - m);
+                res->res_ade = rel_residual(s[3], s[4]) / (double)(n - m);
                 res->mass = s[2];
                 res->substrate = s[5];
                 res->current = s[6];
+                memcpy(u_prev, u, sizeof(double) * d * N);
+                memcpy(c_prev, conc, sizeof(double) * N);
+                m = n;
                 if (res->res_flow < tol_flow && res->res_ade < tol_ade) {
                     conv_f = conv_a = 1;
                     break;

@@ -127,6 +127,42 @@ def test_shear_wave_viscosity(dim, tau):
     assert nu == pytest.approx((tau - 0.5) / 3.0, rel=1e-3)
 
 
+def test_residual_is_mean_change_per_step_since_last_check():
+    """The steady-state residual of a decaying wave has a closed form.  With v^n = a e^(-lam n) s
+    (flow: shear wave, lam = nu k^2; transport: C = C0 + a e^(-lam n) s on a fluid at rest,
+    lam = D k^2), the residual over the checks at 100, 200 and the cap 250 is, at n = 251 steps
+    after the start (one step run before the solve), ||v^251 - v^201|| / (50 ||v^251||)."""
+    L, K, cap = 64, 100, 250
+    x = np.arange(L)
+    s = np.sin(2 * np.pi * x / L)
+    kk = 2 * np.pi / L
+    # flow
+    tau = 0.8
+    o = oracle.Oracle((L, 1), bc=(BC_PERIODIC,) * 3, tau=tau)
+    for k in range(L):
+        o.f[:, k] = oracle.flow_equilibrium(2, 1.0, [0.0, 1e-4 * s[k]])
+    o.step_flow(1)
+    r = o.solve_steady(mode=oracle.SEQUENTIAL, tol_flow=0.0, tol_ade=0.0, max_steps=cap,
+                       check_every=K)
+    lam = (tau - 0.5) / 3.0 * kk * kk
+    assert r.steps_flow == cap
+    assert r.res_flow == pytest.approx((math.exp(50 * lam) - 1.0) / 50, rel=5e-3)
+    # transport
+    tau_c, c0, a0 = 0.7, 1.0, 0.1
+    o = oracle.Oracle((L, 1), bc=(BC_PERIODIC,) * 3, tau=0.8, tau_c=tau_c)
+    for k in range(L):
+        o.g[:, k] = oracle.ade_equilibrium(5, c0 + a0 * s[k], [0.0, 0.0])
+    o.step_coupled(1)
+    r = o.solve_steady(mode=oracle.CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=cap,
+                       check_every=K)
+    lam = (tau_c - 0.5) / 3.0 * kk * kk
+    a = a0 * math.exp(-lam * 251)
+    ss = float((s * s).sum())
+    expect = a * (math.exp(50 * lam) - 1.0) * math.sqrt(ss) / (50 * math.sqrt(L * c0 * c0 + a * a * ss))
+    assert r.res_ade == pytest.approx(expect, rel=5e-3)
+    assert r.res_flow == 0.0  # a fluid at rest: no change and no velocity
+
+
 def test_table1_flow_relaxation_time():
     """Table 1's tau = 0.6706 runs at the lattice viscosity (tau - 1/2)/3 = 0.05687."""
     t1 = golden("table1.json")
