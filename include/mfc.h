@@ -91,11 +91,17 @@ typedef struct {
     int ade_outlet;    /* MFC_OUTLET_ZERO_GRADIENT or MFC_OUTLET_DIRICHLET */
 } mfc_params;
 
+/* Residual of a check at step n: the mean relative change per step since the previous check m,
+ *     r = ||v^n - v^m||_2 / ((n - m) ||v^n||_2)   (sums over the open nodes, in FP64),
+ * for v = u (flow) and v = C (transport).  m is the previous check of the same solve, or, for
+ * the first check, the last step run before the call (every stepping call stores its last
+ * step's fields).  With K = 1 this is the per-step change; a longer interval averages out the
+ * step-to-step rounding jitter of FP32 / FP16 populations near steady state. */
 typedef struct {
-    double tol_flow;   /* flow steady when ||u^n - u^(n-1)|| / ||u^n|| < tol_flow */
-    double tol_ade;    /* transport steady when ||C^n - C^(n-1)|| / ||C^n|| < tol_ade */
+    double tol_flow;   /* flow steady when its residual r < tol_flow */
+    double tol_ade;    /* transport steady when its residual r < tol_ade */
     long max_steps;    /* step cap per solver (sequential) or for both (concurrent) */
-    int check_every;   /* K: residual test every K steps (rounded up to an even number) */
+    int check_every;   /* K >= 1: a check every K steps and at the step cap */
     int mode;          /* MFC_SEQUENTIAL (flow to steady, then transport) or MFC_CONCURRENT */
     double timeout_s;  /* host wall-clock limit; <= 0 for none */
 } mfc_solve_opts;

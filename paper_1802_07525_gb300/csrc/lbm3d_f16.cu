@@ -1,6 +1,8 @@
-// 3-D step and ghost-fill kernels with FP16 population storage.
+// 3-D step, batch-step and ghost-fill kernels with FP16 population storage.
 #define MFC_DIM 3
 #define MFC_ST __half
 #define MFC_STEP_FN launch_step_3d_f16
 #define MFC_FILL_FN launch_fill_ghosts_3d_f16
+#define MFC_BATCH_FN launch_batch_3d_f16
+#define MFC_ARGS_FN step_args_3d_f16
 #include "lbm_launch.cuh"

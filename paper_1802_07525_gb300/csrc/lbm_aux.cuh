@@ -10,24 +10,6 @@ namespace mfc {
 // Lattice sums in FP64, in a fixed order and in two stages spread over many SMs (a single block
 // would be bound by one SM's FP64 rate).  Stage 1: block b adds partials b, b + gridDim.x, ...
 // and writes one partial; stage 2: one block adds those and writes the sums and the residuals.
-__device__ __forceinline__ void block_sum_fp64(double (&acc)[NSUM], double *out)
-{
-    __shared__ double sh[8][NSUM];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int m = 0; m < NSUM; ++m) acc[m] = warp_sum(acc[m]);
-    if (lane == 0) {
-#pragma unroll
-        for (int m = 0; m < NSUM; ++m) sh[warp][m] = acc[m];
-    }
-    __syncthreads();
-    if (threadIdx.x < NSUM) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
-        out[threadIdx.x] = v;
-    }
-}
-
 __global__ void __launch_bounds__(256) finalize_stage1_kernel(const double *partials, int nblocks,
                                                                double *stage1)
 {

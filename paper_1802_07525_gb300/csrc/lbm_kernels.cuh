@@ -91,11 +91,11 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Sum the NSUM per-node terms over the block; thread 0 writes them, as doubles, to
-// partials[block].  Node terms and the sums over a warp and over the block (at most 256 terms)
+// Sum the NSUM per-node terms over the block; threads 0..NSUM-1 write them, as doubles, to
+// dst[0..NSUM).  Node terms and the sums over a warp and over the block (at most 256 terms)
 // are FP32; the sum over the blocks of the lattice is FP64 (finalize kernels).  GB300's FP64
 // rate is a small fraction of its FP32 rate, so per-warp FP64 work would dominate the check step.
-__device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *partials)
+__device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *dst)
 {
     __shared__ float sh[8][NSUM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -110,8 +110,27 @@ __device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *parti
     if (threadIdx.x < NSUM) {
         float v = 0.f;
         for (int w = 0; w < nwarp; ++w) v += sh[w][threadIdx.x];
-        partials[((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)) * NSUM +
-                 threadIdx.x] = (double)v;
+        dst[threadIdx.x] = (double)v;
+    }
+}
+
+// FP64 sum of NSUM values per thread over a block of at most 256 threads (a multiple of 32);
+// threads 0..NSUM-1 write the totals to out[0..NSUM).
+__device__ __forceinline__ void block_sum_fp64(double (&acc)[NSUM], double *out)
+{
+    __shared__ double sh[8][NSUM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) acc[m] = warp_sum(acc[m]);
+    if (lane == 0) {
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) sh[warp][m] = acc[m];
+    }
+    __syncthreads();
+    if (threadIdx.x < NSUM) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        out[threadIdx.x] = v;
     }
 }
 
@@ -242,35 +261,40 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, 
 
 // ---- the step kernel -------------------------------------------------------------------------
 
+// Does the tile of n nodes from (x0, y, z) along x hold a node that writes ghost values?
 template <int DIM>
-__device__ __forceinline__ bool block_on_open_boundary(const Geo &g, const int (&bc)[3])
+__device__ __forceinline__ bool tile_on_open_boundary(const Geo &g, const int (&bc)[3], int x0, int n, int y, int z)
 {
-    bool b = bc[0] != BC_WALL && (blockIdx.x == 0 || (blockIdx.x + 1) * blockDim.x >= (unsigned)g.nx);
-    b = b || (bc[1] != BC_WALL && (blockIdx.y == 0 || blockIdx.y == (unsigned)g.ny - 1));
-    if (DIM == 3) b = b || (bc[2] != BC_WALL && (blockIdx.z == 0 || blockIdx.z == (unsigned)g.nz - 1));
+    bool b = bc[0] != BC_WALL && (x0 == 0 || x0 + n >= g.nx);
+    b = b || (bc[1] != BC_WALL && (y == 0 || y == g.ny - 1));
+    if (DIM == 3) b = b || (bc[2] != BC_WALL && (z == 0 || z == g.nz - 1));
     return b;
 }
 
+// Register caps of the step kernels: 2-D plain steps fit 32 registers (8 blocks of 256 threads
+// per SM), 2-D store/check steps 40; 3-D steps are left uncapped.
+template <int DIM, int MODE> struct StepOccupancy {
+    static constexpr int blocks = DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) : 1;
+};
+
+// One step of node (x0 + threadIdx.x, y, z) of one lattice, in a tile of blockDim.x nodes from
+// (x0, y, z).  Threads with x >= nx return at once, except in check steps, where they compute on
+// a copy of the last node of the row, store nothing and add nothing, so that the whole block
+// joins the reduction.  acc receives the node's check-step terms.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
-__global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) : 1) lbm_step_kernel(const StepArgs<DIM, ST> a)
+__device__ __forceinline__ void step_node(const StepArgs<DIM, ST> &a, int x0, int y, int z, float (&acc)[NSUM])
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM>;
     using LK = Links<DIM>;
     const Geo g = a.geo;
-    float acc[NSUM];
-#pragma unroll
-    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
-
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    // threads past the end of the row: nothing to do, except join the block reduction of a
-    // check step (they compute on a copy of the last node and store nothing)
+    const int x = x0 + threadIdx.x;
     if (MODE != MODE_CHECK && x >= g.nx) return;
     const bool valid = MODE != MODE_CHECK || x < g.nx;
     const long long k = g.at(x < g.nx ? x : g.nx - 1, y, z);
     const uint32_t L = __ldg(a.link + k);
-    const bool ghosts = block_on_open_boundary<DIM>(g, a.bc) && valid && on_open_boundary<DIM>(g, a.bc, x, y, z);
+    const bool ghosts = tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z) && valid &&
+                        on_open_boundary<DIM>(g, a.bc, x, y, z);
     float u[3] = {0.f, 0.f, 0.f};
     // check step: the previous fields of this node (read before this thread overwrites them),
     // issued first so that their latency overlaps the population loads
@@ -400,7 +424,92 @@ __global__ void __launch_bounds__(256, DIM == 2 ? (MODE == MODE_PLAIN ? 8 : 6) :
             a.fld_c[k] = open ? cp : -a.c_ref;
         }
     }
-    if (MODE == MODE_CHECK) block_partials(acc, a.partials);
+}
+
+// One step of one lattice: one thread per node, grid (row / block, ny, nz); one reduction
+// partial per block on check steps.
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
+__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE>::blocks) lbm_step_kernel(const StepArgs<DIM, ST> a)
+{
+    float acc[NSUM];
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
+    step_node<DIM, ST, FLOW, ADE, MODE>(a, blockIdx.x * blockDim.x, blockIdx.y, blockIdx.z, acc);
+    if (MODE == MODE_CHECK)
+        block_partials(acc, a.partials + ((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y *
+                                                                                  blockIdx.z)) * NSUM);
+}
+
+// ---- many lattices in one launch -------------------------------------------------------------
+// A tile is one block's worth of nodes along x of one row of one lattice (instance).  The tile
+// table lists the tiles of every instance of the launch, instance after instance; a fixed grid
+// of blocks (a few per SM) walks it with a stride of the grid, so the launch shape does not
+// depend on which instances are active.  Each instance slot holds two argument blocks, for the
+// two buffer parities; a step uses the one of its parity.
+struct Tile {
+    int slot, x0, y, z;
+};
+
+template <int DIM, typename ST> struct BatchArgs {
+    const StepArgs<DIM, ST> *inst;  // [2 * slot + parity]
+    const Tile *tiles;              // tile table
+    const int *ntiles;              // tiles in the table (device value, set before the launch)
+    double *partials;               // NSUM per tile (check steps)
+    int parity;
+};
+
+// The tile loop and the shared argument block take registers of their own: 2-D batch steps are
+// capped at 48 registers (5 blocks of 256 threads per SM), where they do not spill.
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
+__global__ void __launch_bounds__(256, DIM == 2 ? 5 : 1) lbm_batch_kernel(const BatchArgs<DIM, ST> b)
+{
+    static_assert(sizeof(StepArgs<DIM, ST>) % 4 == 0, "argument block copied as 32-bit words");
+    __shared__ StepArgs<DIM, ST> sa;  // arguments of the instance of the current tile
+    constexpr int WORDS = (int)(sizeof(StepArgs<DIM, ST>) / 4);
+    const int n = *b.ntiles;
+    int cur = -1;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const Tile tile = b.tiles[t];
+        if (tile.slot != cur) {  // uniform over the block: every thread reads the same entry
+            __syncthreads();     // the previous instance's arguments are no longer read
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.inst + 2 * tile.slot + b.parity);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+            for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            cur = tile.slot;
+        }
+        float acc[NSUM];
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
+        step_node<DIM, ST, FLOW, ADE, MODE>(sa, tile.x0, tile.y, tile.z, acc);
+        if (MODE == MODE_CHECK) {
+            block_partials(acc, b.partials + (size_t)t * NSUM);
+            __syncthreads();  // the reduction's shared memory is reused by the next tile
+        }
+    }
+}
+
+// Per instance slot s, the sums over its tiles [range[s].x, range[s].y) of the launch, in FP64
+// and in a fixed order, and the two residuals: results[s * NRESULT ...].  One block per slot.
+__device__ __forceinline__ void batch_finalize_slot(const int2 range, const double *partials,
+                                                    double *res)
+{
+    double acc[NSUM];
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0;
+    for (int t = range.x + threadIdx.x; t < range.y; t += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) acc[m] += partials[(size_t)t * NSUM + m];
+    }
+    __shared__ double r[NSUM];
+    block_sum_fp64(acc, r);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int m = 0; m < NSUM; ++m) res[m] = r[m];
+        res[RES_FLOW] = r[SUM_U2] > 0.0 ? sqrt(r[SUM_DU2] / r[SUM_U2]) : (r[SUM_DU2] > 0.0 ? INFINITY : 0.0);
+        res[RES_ADE] = r[SUM_C2] > 0.0 ? sqrt(r[SUM_DC2] / r[SUM_C2]) : (r[SUM_DC2] > 0.0 ? INFINITY : 0.0);
+    }
 }
 
 // Write the ghost cells of the current buffers (a.fdst, a.gdst) from the state they hold, after

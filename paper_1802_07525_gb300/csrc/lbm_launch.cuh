@@ -1,6 +1,8 @@
-// Launchers of the step and ghost-fill kernels for one dimension (MFC_DIM) and one storage type
-// (MFC_ST), included by one translation unit per pair so that the instantiations compile in
-// parallel.
+// Launchers of the step, batch-step and ghost-fill kernels for one dimension (MFC_DIM) and one
+// storage type (MFC_ST), included by one translation unit per pair so that the instantiations
+// compile in parallel.
+#include <string.h>
+
 #include "mfc_internal.h"
 
 #ifndef MFC_DIM
@@ -59,6 +61,30 @@ cudaError_t MFC_STEP_FN(StepHost &h, cudaStream_t s)
     case KIND_FLOW: return launch_mode<true, false>(a, h, s);
     default: return launch_mode<false, true>(a, h, s);
     }
+}
+
+size_t MFC_ARGS_FN(const StepHost &h, void *out)
+{
+    const StepArgs<D, ST> a = make_args(h);
+    if (out) memcpy(out, &a, sizeof a);
+    return sizeof a;
+}
+
+// Coupled steps only: a batch advances flow and transport of every instance together.
+cudaError_t MFC_BATCH_FN(const BatchHost &h, cudaStream_t s)
+{
+    BatchArgs<D, ST> b;
+    b.inst = static_cast<const StepArgs<D, ST> *>(h.inst);
+    b.tiles = h.tiles;
+    b.ntiles = h.ntiles;
+    b.partials = h.partials;
+    b.parity = h.parity;
+    switch (h.mode) {
+    case MODE_PLAIN: lbm_batch_kernel<D, ST, true, true, MODE_PLAIN><<<h.grid, h.block, 0, s>>>(b); break;
+    case MODE_WRITE: lbm_batch_kernel<D, ST, true, true, MODE_WRITE><<<h.grid, h.block, 0, s>>>(b); break;
+    default: lbm_batch_kernel<D, ST, true, true, MODE_CHECK><<<h.grid, h.block, 0, s>>>(b); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t MFC_FILL_FN(const StepHost &h, cudaStream_t s)

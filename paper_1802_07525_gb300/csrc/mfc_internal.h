@@ -33,6 +33,17 @@ struct StepHost {
     float bb_in[19], gin_dev[7], gout_dev[7];
 };
 
+// One launch of the batch step kernel over a tile table (coupled steps).
+struct BatchHost {
+    int dim, half, mode;
+    const void *inst;   // device array of per-slot argument blocks, two per slot
+    const Tile *tiles;  // device tile table
+    const int *ntiles;  // device tile count
+    double *partials;   // NSUM per tile
+    int parity;
+    int grid, block;
+};
+
 cudaError_t launch_step_2d_f32(StepHost &h, cudaStream_t s);
 cudaError_t launch_step_2d_f16(StepHost &h, cudaStream_t s);
 cudaError_t launch_step_3d_f32(StepHost &h, cudaStream_t s);
@@ -42,6 +53,29 @@ cudaError_t launch_fill_ghosts_2d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_2d_f16(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f16(const StepHost &h, cudaStream_t s);
+
+cudaError_t launch_batch_2d_f32(const BatchHost &h, cudaStream_t s);
+cudaError_t launch_batch_2d_f16(const BatchHost &h, cudaStream_t s);
+cudaError_t launch_batch_3d_f32(const BatchHost &h, cudaStream_t s);
+cudaError_t launch_batch_3d_f16(const BatchHost &h, cudaStream_t s);
+// The device argument block of a step (StepArgs of the lattice's dimension and storage type)
+// written to out (when not null); returns its size in bytes.
+size_t step_args_2d_f32(const StepHost &h, void *out);
+size_t step_args_2d_f16(const StepHost &h, void *out);
+size_t step_args_3d_f32(const StepHost &h, void *out);
+size_t step_args_3d_f16(const StepHost &h, void *out);
+
+inline cudaError_t launch_batch(const BatchHost &h, cudaStream_t s)
+{
+    if (h.dim == 2) return h.half ? launch_batch_2d_f16(h, s) : launch_batch_2d_f32(h, s);
+    return h.half ? launch_batch_3d_f16(h, s) : launch_batch_3d_f32(h, s);
+}
+
+inline size_t step_args(const StepHost &h, void *out)
+{
+    if (h.dim == 2) return h.half ? step_args_2d_f16(h, out) : step_args_2d_f32(h, out);
+    return h.half ? step_args_3d_f16(h, out) : step_args_3d_f32(h, out);
+}
 
 inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
 {

@@ -319,14 +319,14 @@ mfc_status fill_ghosts(mfc_lattice *L)
     return MFC_OK;
 }
 
-// Queue n steps ending with a residual check (n >= 2) or with a field store (n == 1).
+// Queue n >= 1 steps ending with a residual check (which compares the fields with those stored
+// by the last step before the block, and stores its own) or with a plain field store.
 mfc_status enqueue_block(mfc_lattice *L, int kind, int n, bool check)
 {
     int nb = L->nblocks;
     for (int s = 0; s < n; ++s) {
         int mode = MODE_PLAIN;
         if (s == n - 1) mode = check ? MODE_CHECK : MODE_WRITE;
-        else if (s == n - 2 && check) mode = MODE_WRITE;
         mfc_status st = enqueue_step(L, kind, mode, &nb);
         if (st != MFC_OK) return st;
     }
@@ -345,7 +345,7 @@ void drop_graphs(mfc_lattice *L)
     L->graphs.clear();
 }
 
-// The graph of K (even) steps ending with a check, for the current buffer parity.
+// The graph of K steps ending with a check, for the current buffer parity.
 mfc_status graph_for(mfc_lattice *L, int kind, int K, cudaGraphExec_t *out)
 {
     for (auto &g : L->graphs)
@@ -403,7 +403,10 @@ double now_s()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Run one solver (or both, concurrently) to steady state.
+// Run one solver (or both, concurrently) to steady state.  Steps run in blocks of K ending with a
+// check; the residual of a check is the mean relative change per step since the previous one,
+// ||v^n - v^m|| / ((n - m) ||v^n||), where the fields of step m were stored by the previous
+// check, or, for the first block, by the last step run before the call.
 mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, long max_steps, int K,
                      double deadline, long *steps, double *res_f, double *res_a, bool *converged)
 {
@@ -421,29 +424,27 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
             if (kind != KIND_ADE && (K & 1)) L->fcur ^= 1;
             if (kind != KIND_FLOW && (K & 1)) L->gcur ^= 1;
         } else {
-            st = enqueue_block(L, kind, n, n >= 2);
+            st = enqueue_block(L, kind, n, true);
             if (st != MFC_OK) return st;
         }
         bool to = false;
         st = wait_done(L, deadline, &to);
         if (st != MFC_OK) return st;
         *steps += n;
-        if (n >= 2) {
-            const double *r = L->results_h;
-            if (kind != KIND_ADE) *res_f = r[RES_FLOW];
-            if (kind != KIND_FLOW) {
-                *res_a = r[RES_ADE];
-                L->last_current = r[SUM_CURRENT];
-            }
-            if (r[SUM_BAD] > 0.0 || !isfinite(r[SUM_MASS]) || !isfinite(r[SUM_C]) ||
-                isnan(r[RES_FLOW]) || isnan(r[RES_ADE]))
-                return MFC_ERR_NONFINITE;
-            const bool okf = kind == KIND_ADE || r[RES_FLOW] < tol_flow;
-            const bool oka = kind == KIND_FLOW || r[RES_ADE] < tol_ade;
-            if (okf && oka) {
-                *converged = true;
-                return MFC_OK;
-            }
+        const double *r = L->results_h;
+        const double rf = r[RES_FLOW] / n, ra = r[RES_ADE] / n;
+        if (kind != KIND_ADE) *res_f = rf;
+        if (kind != KIND_FLOW) {
+            *res_a = ra;
+            L->last_current = r[SUM_CURRENT];
+        }
+        if (r[SUM_BAD] > 0.0 || !isfinite(r[SUM_MASS]) || !isfinite(r[SUM_C]) || isnan(rf) || isnan(ra))
+            return MFC_ERR_NONFINITE;
+        const bool okf = kind == KIND_ADE || rf < tol_flow;
+        const bool oka = kind == KIND_FLOW || ra < tol_ade;
+        if (okf && oka) {
+            *converged = true;
+            return MFC_OK;
         }
         if (to) return MFC_ERR_TIMEOUT;
     }
@@ -711,8 +712,7 @@ MFC_API mfc_status mfc_solve_steady(mfc_lattice *L, const mfc_solve_opts *opts, 
     if (opts->max_steps < 0 || opts->check_every < 1 || !(opts->tol_flow >= 0.0) ||
         !(opts->tol_ade >= 0.0) || (opts->mode != MFC_SEQUENTIAL && opts->mode != MFC_CONCURRENT))
         return fail(L, MFC_ERR_ARG, "bad solve options");
-    int K = opts->check_every < 2 ? 2 : opts->check_every;
-    if (K & 1) ++K;
+    const int K = opts->check_every;
     const double deadline = opts->timeout_s > 0.0 ? now_s() + opts->timeout_s : 0.0;
     mfc_solve_result r;
     memset(&r, 0, sizeof r);

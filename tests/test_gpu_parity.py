@@ -174,18 +174,19 @@ def test_channel_128x64_steady_fields_and_current(P, mode):
 
 def test_residual_sums_match_oracle_sums(P):
     """The FP64 reductions of a check step agree with the oracle's sums of the same fields:
-    400 fused steps, then a 2-step solve block (store fields at 401, compare at 402)."""
+    400 fused steps (fields stored at 400), then a 2-step solve block that compares the fields
+    of step 402 with those of step 400; its residuals are per step."""
     w = mi.channel_128x64()
     g, o = pair(P, w.shape, w.cls, **channel_kw(w))
     g.step_coupled(400)
     r = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=2, check_every=2)
-    o.step_coupled(401)
+    o.step_coupled(400)
     u1, c1 = o.u.copy(), o.conc.copy()
-    o.step_coupled(1)
+    o.step_coupled(2)
     s = o.sums(u1, c1)
     assert r.status == P.MFC_NOT_CONVERGED and r.steps_flow == 2
-    assert r.res_flow == pytest.approx(np.sqrt(s[0] / s[1]), rel=1e-3)
-    assert r.res_ade == pytest.approx(np.sqrt(s[3] / s[4]), rel=1e-3)
+    assert r.res_flow == pytest.approx(np.sqrt(s[0] / s[1]) / 2, rel=1e-3)
+    assert r.res_ade == pytest.approx(np.sqrt(s[3] / s[4]) / 2, rel=1e-3)
     assert r.current == pytest.approx(s[6], rel=1e-5)
     assert r.mass == pytest.approx(s[2], rel=1e-7)
     assert r.substrate == pytest.approx(s[5], rel=1e-5)
