@@ -61,7 +61,8 @@ typedef enum {
     MFC_NOT_CONVERGED = 5,    /* step cap reached before the residuals fell below tolerance */
     MFC_ERR_NONFINITE = 6,    /* a residual, mass or current sum was not finite */
     MFC_ERR_TIMEOUT = 7,      /* the host-side wall-clock limit of a solve was reached */
-    MFC_ERR_STATE = 8         /* call not valid in the object's current state */
+    MFC_ERR_STATE = 8,        /* call not valid in the object's current state */
+    MFC_PENDING = 9           /* a batch request has not finished yet */
 } mfc_status;
 
 enum { MFC_BC_WALL = 0, MFC_BC_PERIODIC = 1, MFC_BC_INOUT = 2 };
@@ -222,6 +223,85 @@ MFC_API mfc_status mfc_field_sums_noalloc(long long n, int dim, const uint8_t *n
                                           const double *rho, const double *u, const double *u_prev,
                                           const double *c, const double *c_prev, double k_sink,
                                           double *out, void *stream);
+
+/* ---- batches: many steady solves sharing the GPU (continuous batching) ------------------ */
+
+/* A batch runs steady solves (mfc_solve_steady with MFC_CONCURRENT) of many lattices at once.
+ * Requests are admitted first come, first served, as instance slots and device memory free up
+ * (each request's device memory, mfc_lattice_bytes plus the read-back staging when fields are
+ * asked for, counts against budget_bytes); admitted instances stay resident on the device and
+ * advance together, every lattice of every instance in one launch per step and dimension (a
+ * fixed grid of a few blocks per SM walking a tile table of all instances' rows), in CUDA-graph
+ * replays of K steps that end with every instance's residual check.  A finished instance
+ * (converged, at its step cap, timed out or non-finite) leaves at the end of its block; its
+ * fields are copied to the caller's buffers, its memory goes back to the batch's pool, and
+ * waiting requests are admitted before the next block.
+ *
+ * What a request gets does not depend on what else runs: every instance steps and checks
+ * exactly as it would alone in a batch with the same K and block, bit for bit.  Against
+ * mfc_solve_steady with check_every = K, the checks fall on the same steps; the step cap is
+ * taken in whole blocks (a batch solve ends at the first check at or after max_steps).
+ *
+ * Threads: submit, poll, wait and stats may be called from any thread.  The engine runs either
+ * on the caller's thread (mfc_batch_run, until nothing is queued or running) or on a library
+ * thread (mfc_batch_start ... mfc_batch_stop).  All device work runs on the batch's stream. */
+typedef struct mfc_batch mfc_batch; /* opaque */
+
+typedef struct {
+    size_t budget_bytes;  /* device memory for instances; 0 = 90% of the free memory at create */
+    int precision;        /* MFC_FP32 or MFC_FP16_DEV, for every instance */
+    int check_every;      /* K (even, >= 2; odd values are rounded up); 0 = chosen by the autotuner */
+    int block;            /* threads per tile: 64, 128 or 256; 0 = chosen by the autotuner */
+    int max_instances;    /* instance slots, 1..4096; 0 = 256 */
+    void *stream;         /* cudaStream_t, or NULL for a library-owned stream */
+} mfc_batch_opts;
+
+typedef struct {
+    mfc_solve_result result; /* as mfc_solve_steady fills it (steps in whole blocks) */
+    double t_submit;         /* mfc_clock() at submission */
+    double t_admit;          /* when the instance was created on the device */
+    double t_done;           /* when the result and fields were ready */
+} mfc_batch_result;
+
+typedef struct {
+    long long submitted, completed, running, queued;
+    long long blocks;           /* graph replays run */
+    long long instance_steps;   /* sum over instances of the steps they took */
+    size_t bytes_in_use, bytes_peak, budget_bytes;
+    int check_every, block, grid; /* the launch the batch runs (after autotuning) */
+} mfc_batch_stats;
+
+MFC_API mfc_status mfc_batch_create(const mfc_batch_opts *opts, mfc_batch **out);
+/* Stops the engine thread, abandons unfinished requests and frees every instance. */
+MFC_API mfc_status mfc_batch_destroy(mfc_batch *batch);
+/* Queue a steady solve.  desc: the lattice (its precision must be the batch's; its stream is
+ * ignored); params as for mfc_create_lattice; node_class: N classes, copied during the call;
+ * opts: tolerances, max_steps and timeout_s (from admission) as for mfc_solve_steady, mode must
+ * be MFC_CONCURRENT, check_every is ignored (the batch's K applies).  rho, u, c: optional host
+ * buffers (N, dim*N, N doubles, as mfc_read_fields fills them) that the batch fills when the
+ * solve ends; they must stay valid until then.  *ticket identifies the request.  Fails with
+ * MFC_ERR_ARG for a bad request and MFC_ERR_OOM_BUDGET when it can never fit the budget. */
+MFC_API mfc_status mfc_batch_submit(mfc_batch *batch, const mfc_lattice_desc *desc,
+                                    const mfc_params *params, const uint8_t *node_class,
+                                    const mfc_solve_opts *opts, double *rho, double *u, double *c,
+                                    long long *ticket);
+/* MFC_PENDING while the request runs or waits; otherwise the solve's status (as
+ * mfc_solve_steady returns it) with *out filled, and the ticket is released. */
+MFC_API mfc_status mfc_batch_poll(mfc_batch *batch, long long ticket, mfc_batch_result *out);
+/* As poll, waiting up to timeout_s seconds (< 0: no limit) for the request to finish. */
+MFC_API mfc_status mfc_batch_wait(mfc_batch *batch, long long ticket, double timeout_s,
+                                  mfc_batch_result *out);
+/* Run the engine on the calling thread until no request is queued or running. */
+MFC_API mfc_status mfc_batch_run(mfc_batch *batch);
+/* Run the engine on a library thread, which admits requests as they arrive. */
+MFC_API mfc_status mfc_batch_start(mfc_batch *batch);
+/* Stop the engine thread at the end of its current block (requests stay queued or resident). */
+MFC_API mfc_status mfc_batch_stop(mfc_batch *batch);
+MFC_API mfc_status mfc_batch_get_stats(mfc_batch *batch, mfc_batch_stats *out);
+/* Text of the batch's last error. */
+MFC_API const char *mfc_batch_last_error(mfc_batch *batch);
+/* Seconds on the library's monotonic clock (the clock of the batch time stamps). */
+MFC_API double mfc_clock(void);
 
 /* ---- introspection --------------------------------------------------------------------- */
 

@@ -5,4 +5,5 @@
 #define MFC_FILL_FN launch_fill_ghosts_2d_f16
 #define MFC_BATCH_FN launch_batch_2d_f16
 #define MFC_ARGS_FN step_args_2d_f16
+#define MFC_OCC_FN batch_occupancy_2d_f16
 #include "lbm_launch.cuh"

@@ -87,6 +87,18 @@ cudaError_t MFC_BATCH_FN(const BatchHost &h, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Resident blocks per SM of the plain batch step at `block` threads.
+int MFC_OCC_FN(int block)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<D, ST, true, true, MODE_PLAIN>, block, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 cudaError_t MFC_FILL_FN(const StepHost &h, cudaStream_t s)
 {
     const StepArgs<D, ST> a = make_args(h);

@@ -65,6 +65,17 @@ size_t step_args_2d_f16(const StepHost &h, void *out);
 size_t step_args_3d_f32(const StepHost &h, void *out);
 size_t step_args_3d_f16(const StepHost &h, void *out);
 
+int batch_occupancy_2d_f32(int block);
+int batch_occupancy_2d_f16(int block);
+int batch_occupancy_3d_f32(int block);
+int batch_occupancy_3d_f16(int block);
+
+inline int batch_occupancy(int dim, int half, int block)
+{
+    if (dim == 2) return half ? batch_occupancy_2d_f16(block) : batch_occupancy_2d_f32(block);
+    return half ? batch_occupancy_3d_f16(block) : batch_occupancy_3d_f32(block);
+}
+
 inline cudaError_t launch_batch(const BatchHost &h, cudaStream_t s)
 {
     if (h.dim == 2) return h.half ? launch_batch_2d_f16(h, s) : launch_batch_2d_f32(h, s);

@@ -19,6 +19,7 @@
 #include "../../include/mfc.h"
 #include "lbm_aux.cuh"
 #include "mfc_internal.h"
+#include "runtime.h"
 
 namespace mfc {
 
@@ -78,48 +79,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct GraphEntry {
-    int kind, K, fpar, gpar;
-    cudaGraphExec_t exec;
-};
-
 }  // namespace
-
-struct mfc_lattice {
-    mfc_lattice_desc desc;
-    mfc_params prm;
-    int dim = 2, qf = 9, qa = 5, half = 0;
-    int nx = 1, ny = 1, nz = 1;
-    Geo geo;
-    long long N = 0;
-    size_t st_bytes = 4;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    void *f[2] = {nullptr, nullptr};
-    void *g[2] = {nullptr, nullptr};
-    int fcur = 0, gcur = 0;  // buffer holding the current state (read by the next step)
-    void *link = nullptr;
-    int link32 = 0;
-    uint8_t *cls_cur = nullptr, *cls_tmp = nullptr;
-    float *fld_rho = nullptr, *fld_u = nullptr, *fld_c = nullptr;
-    double *partials = nullptr;
-    double *results_d = nullptr, *results_h = nullptr;
-    unsigned long long *counts_d = nullptr, *counts_h = nullptr;
-    double *staging = nullptr;
-    size_t staging_bytes = 0;
-    cudaEvent_t done = nullptr;
-    float c_ref = 1.0f;
-    int grid = 1, block = DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
-
-
-    std::vector<GraphEntry> graphs;
-    long flow_open = 0, ade_open = 0;
-    double last_current = 0.0;
-    size_t bytes = 0;
-    std::string err;
-    mfc_status sticky = MFC_OK;
-};
 
 namespace {
 
@@ -251,7 +211,9 @@ int max_launch_blocks(const Layout &l)
     return (l.geo.nx + 127) / 128 * l.geo.ny * l.geo.nz;
 }
 
-void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
+}  // namespace
+
+void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
 {
     memset(h, 0, sizeof *h);
     h->dim = L->dim;
@@ -292,6 +254,8 @@ void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
         h->gout_dev[i] = (float)(w * p.c_out * (1.0 + ci * p.u_in * inv_cs2) - w * L->c_ref);
     }
 }
+
+namespace {
 
 // Queue one step of `kind` and swap the buffers it wrote; *nblocks receives the blocks (and
 // reduction partials) of the launch.
@@ -398,10 +362,14 @@ mfc_status wait_done(mfc_lattice *L, double deadline_s, bool *timed_out)
     }
 }
 
-double now_s()
+}  // namespace
+
+double mfc::now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+namespace {
 
 // Run one solver (or both, concurrently) to steady state.  Steps run in blocks of K ending with a
 // check; the residual of a check is the mean relative change per step since the previous one,
@@ -451,24 +419,56 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
     return MFC_OK;
 }
 
+// Device allocation of a lattice buffer, zero-filled (ghosts and padding start defined): from
+// the lattice's pool on its stream, or with cudaMalloc.
+bool dev_alloc(mfc_lattice *L, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (L->pool) {
+        if (cudaMallocFromPoolAsync(p, bytes, L->pool, L->stream) != cudaSuccess ||
+            cudaMemsetAsync(*p, 0, bytes, L->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    if (cudaMemset(*p, 0, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+void dev_free(mfc_lattice *L, void *p)
+{
+    if (!p) return;
+    if (L->pool) cudaFreeAsync(p, L->stream);
+    else cudaFree(p);
+}
+
 void release(mfc_lattice *L)
 {
     if (!L) return;
     drop_graphs(L);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(L->f[b]);
-        cudaFree(L->g[b]);
+        dev_free(L, L->f[b]);
+        dev_free(L, L->g[b]);
     }
-    cudaFree(L->link);
-    cudaFree(L->cls_cur);
-    cudaFree(L->cls_tmp);
-    cudaFree(L->fld_rho);
-    cudaFree(L->fld_u);
-    cudaFree(L->fld_c);
-    cudaFree(L->partials);
-    cudaFree(L->results_d);
-    cudaFree(L->counts_d);
-    cudaFree(L->staging);
+    dev_free(L, L->link);
+    dev_free(L, L->cls_cur);
+    dev_free(L, L->cls_tmp);
+    dev_free(L, L->fld_rho);
+    dev_free(L, L->fld_u);
+    dev_free(L, L->fld_c);
+    dev_free(L, L->partials);
+    dev_free(L, L->results_d);
+    dev_free(L, L->counts_d);
+    dev_free(L, L->staging);
     if (L->results_h) cudaFreeHost(L->results_h);
     if (L->counts_h) cudaFreeHost(L->counts_h);
     if (L->done) cudaEventDestroy(L->done);
@@ -478,13 +478,12 @@ void release(mfc_lattice *L)
 mfc_status ensure_staging(mfc_lattice *L, size_t bytes)
 {
     if (L->staging_bytes >= bytes) return MFC_OK;
-    cudaFree(L->staging);
+    dev_free(L, L->staging);
     L->staging = nullptr;
     L->staging_bytes = 0;
-    if (cudaMalloc(&L->staging, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(L, MFC_ERR_OOM, "staging allocation failed");
-    }
+    void *p = nullptr;
+    if (!dev_alloc(L, &p, bytes)) return fail(L, MFC_ERR_OOM, "staging allocation failed");
+    L->staging = static_cast<double *>(p);
     L->staging_bytes = bytes;
     return MFC_OK;
 }
@@ -524,6 +523,125 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
 
 }  // namespace
 
+mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *params, cudaMemPool_t pool,
+                               mfc_lattice **out, std::string *why_out)
+{
+    std::string &why = *why_out;
+    if (!out) { why = "out is NULL"; return MFC_ERR_ARG; }
+    *out = nullptr;
+    mfc_status st = check_desc(desc, &why);
+    if (st == MFC_OK) st = check_params(params, &why);
+    if (st != MFC_OK) return st;
+    if (pool && !desc->stream) { why = "a pooled lattice needs a stream"; return MFC_ERR_ARG; }
+
+    int ndev = 0;
+    cudaError_t de = cudaGetDeviceCount(&ndev);
+    if (de != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        why = std::string("no CUDA device: ") + cudaGetErrorString(de);
+        return MFC_ERR_CUDA;
+    }
+    mfc_lattice *L = new (std::nothrow) mfc_lattice();
+    if (!L) { why = "host allocation failed"; return MFC_ERR_OOM; }
+    L->pool = pool;
+    L->desc = *desc;
+    if (desc->dim == 2) {
+        L->desc.nz = 1;
+        L->desc.bc[2] = MFC_BC_PERIODIC;
+    }
+    L->prm = *params;
+    Layout l = layout_of(desc);
+    L->dim = l.dim; L->qf = l.qf; L->qa = l.qa;
+    L->geo = l.geo;
+    L->nx = l.geo.nx; L->ny = l.geo.ny; L->nz = l.geo.nz;
+    L->N = l.N;
+    L->st_bytes = l.st;
+    L->half = desc->precision == MFC_FP16_DEV;
+    L->link32 = desc->dim == 3;
+    // transport storage offset: 0, so that the no-substrate start state is stored exactly
+    L->c_ref = 0.0f;
+    cudaGetDevice(&L->device);
+    L->block = DEFAULT_BLOCK;
+    L->max_blocks = max_launch_blocks(l);
+    choose_launch(L);
+
+    // the stream first: pooled buffers are allocated on it
+    cudaError_t e = cudaSuccess;
+    if (desc->stream) {
+        L->stream = (cudaStream_t)desc->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            L->stream = nullptr;
+            why = std::string("create: ") + cudaGetErrorString(e);
+            delete L;
+            return MFC_ERR_CUDA;
+        }
+        L->own_stream = true;
+    }
+    auto dalloc = [&](void **p, size_t bytes) -> bool {
+        if (!dev_alloc(L, p, bytes)) return false;
+        L->bytes += bytes;
+        return true;
+    };
+    const long long P = l.geo.plane;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && dalloc(&L->f[b], (size_t)l.qf * P * l.st);
+        ok = ok && dalloc(&L->g[b], (size_t)l.qa * P * l.st);
+    }
+    ok = ok && dalloc(&L->link, (size_t)P * l.link_bytes);
+    ok = ok && dalloc((void **)&L->cls_cur, round_up((size_t)l.N, 256));
+    ok = ok && dalloc((void **)&L->cls_tmp, round_up((size_t)l.N, 256));
+    ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
+    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
+    ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
+    // per-block partials, then the stage-1 sums of the finalize
+    ok = ok && dalloc((void **)&L->partials, ((size_t)L->max_blocks + FINAL_STAGE1_MAX) * NSUM * sizeof(double));
+    ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
+    ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
+    if (!ok) {
+        release(L);
+        delete L;
+        why = "device allocation failed";
+        return MFC_ERR_OOM;
+    }
+    e = cudaHostAlloc((void **)&L->results_h, NRESULT * sizeof(double), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&L->counts_h, 2 * sizeof(unsigned long long), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        why = std::string("create: ") + cudaGetErrorString(e);
+        release(L);
+        delete L;
+        return MFC_ERR_CUDA;
+    }
+    memset(L->results_h, 0, NRESULT * sizeof(double));
+    // every node open, rest state
+    e = cudaMemsetAsync(L->cls_cur, 0, round_up((size_t)l.N, 256), L->stream);
+    if (e != cudaSuccess) {
+        why = std::string("create: ") + cudaGetErrorString(e);
+        release(L);
+        delete L;
+        return MFC_ERR_CUDA;
+    }
+    st = apply_geometry(L, L->cls_cur, 1);
+    if (st != MFC_OK) {
+        why = L->err;
+        release(L);
+        delete L;
+        return st;
+    }
+    *out = L;
+    return MFC_OK;
+}
+
+mfc_status mfc::validate_lattice(const mfc_lattice_desc *desc, const mfc_params *params, std::string *why)
+{
+    mfc_status st = check_desc(desc, why);
+    if (st == MFC_OK) st = check_params(params, why);
+    return st;
+}
+
 extern "C" {
 
 MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
@@ -547,108 +665,8 @@ MFC_API mfc_status mfc_create_lattice(const mfc_lattice_desc *desc, const mfc_pa
                                       mfc_lattice **out)
 {
     std::string why;
-    if (!out) return fail(nullptr, MFC_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    mfc_status st = check_desc(desc, &why);
-    if (st == MFC_OK) st = check_params(params, &why);
+    mfc_status st = lattice_create(desc, params, nullptr, out, &why);
     if (st != MFC_OK) return fail(nullptr, st, why);
-
-    int ndev = 0;
-    cudaError_t de = cudaGetDeviceCount(&ndev);
-    if (de != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return fail(nullptr, MFC_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(de));
-    }
-    mfc_lattice *L = new (std::nothrow) mfc_lattice();
-    if (!L) return fail(nullptr, MFC_ERR_OOM, "host allocation failed");
-    L->desc = *desc;
-    if (desc->dim == 2) {
-        L->desc.nz = 1;
-        L->desc.bc[2] = MFC_BC_PERIODIC;
-    }
-    L->prm = *params;
-    Layout l = layout_of(desc);
-    L->dim = l.dim; L->qf = l.qf; L->qa = l.qa;
-    L->geo = l.geo;
-    L->nx = l.geo.nx; L->ny = l.geo.ny; L->nz = l.geo.nz;
-    L->N = l.N;
-    L->st_bytes = l.st;
-    L->half = desc->precision == MFC_FP16_DEV;
-    L->link32 = desc->dim == 3;
-    // transport storage offset: 0, so that the no-substrate start state is stored exactly
-    L->c_ref = 0.0f;
-    cudaGetDevice(&L->device);
-    L->block = DEFAULT_BLOCK;
-    L->max_blocks = max_launch_blocks(l);
-    choose_launch(L);
-
-    auto dalloc = [&](void **p, size_t bytes) -> bool {
-        if (cudaMalloc(p, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        if (cudaMemset(*p, 0, bytes) != cudaSuccess) {  // ghosts and padding start defined
-            cudaGetLastError();
-            return false;
-        }
-        L->bytes += bytes;
-        return true;
-    };
-    const long long P = l.geo.plane;
-    bool ok = true;
-    for (int b = 0; b < 2 && ok; ++b) {
-        ok = ok && dalloc(&L->f[b], (size_t)l.qf * P * l.st);
-        ok = ok && dalloc(&L->g[b], (size_t)l.qa * P * l.st);
-    }
-    ok = ok && dalloc(&L->link, (size_t)P * l.link_bytes);
-    ok = ok && dalloc((void **)&L->cls_cur, round_up((size_t)l.N, 256));
-    ok = ok && dalloc((void **)&L->cls_tmp, round_up((size_t)l.N, 256));
-    ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
-    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
-    ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
-    // per-block partials, then the stage-1 sums of the finalize
-    ok = ok && dalloc((void **)&L->partials, ((size_t)L->max_blocks + FINAL_STAGE1_MAX) * NSUM * sizeof(double));
-    ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
-    ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
-    if (!ok) {
-        release(L);
-        delete L;
-        return fail(nullptr, MFC_ERR_OOM, "device allocation failed");
-    }
-    cudaError_t e = cudaHostAlloc((void **)&L->results_h, NRESULT * sizeof(double), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&L->counts_h, 2 * sizeof(unsigned long long), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) {
-        if (desc->stream) {
-            L->stream = (cudaStream_t)desc->stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
-            L->own_stream = true;
-        }
-    }
-    if (e != cudaSuccess) {
-        std::string msg = std::string("create: ") + cudaGetErrorString(e);
-        release(L);
-        delete L;
-        return fail(nullptr, MFC_ERR_CUDA, msg);
-    }
-    memset(L->results_h, 0, NRESULT * sizeof(double));
-    // every node open, rest state
-    e = cudaMemsetAsync(L->cls_cur, 0, round_up((size_t)l.N, 256), L->stream);
-    if (e != cudaSuccess) {
-        std::string msg = std::string("create: ") + cudaGetErrorString(e);
-        release(L);
-        delete L;
-        return fail(nullptr, MFC_ERR_CUDA, msg);
-    }
-    st = apply_geometry(L, L->cls_cur, 1);
-    if (st != MFC_OK) {
-        std::string msg = L->err;
-        release(L);
-        delete L;
-        return fail(nullptr, st, msg);
-    }
-    *out = L;
     return MFC_OK;
 }
 
@@ -916,6 +934,7 @@ MFC_API const char *mfc_status_string(mfc_status s)
     case MFC_ERR_NONFINITE: return "non-finite residual, mass or current";
     case MFC_ERR_TIMEOUT: return "wall-clock limit reached";
     case MFC_ERR_STATE: return "invalid state";
+    case MFC_PENDING: return "pending";
     }
     return "unknown status";
 }

@@ -1,0 +1,72 @@
+// Host-side lattice object shared by the single-lattice C ABI (runtime.cu) and the batch engine
+// (batch.cu).  Not part of the public interface.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mfc.h"
+#include "mfc_internal.h"
+
+namespace mfc {
+
+struct GraphEntry {
+    int kind, K, fpar, gpar;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace mfc
+
+struct mfc_lattice {
+    mfc_lattice_desc desc;
+    mfc_params prm;
+    int dim = 2, qf = 9, qa = 5, half = 0;
+    int nx = 1, ny = 1, nz = 1;
+    mfc::Geo geo;
+    long long N = 0;
+    size_t st_bytes = 4;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // stream-ordered pool the device buffers come from (batch instances), or null (cudaMalloc)
+    cudaMemPool_t pool = nullptr;
+    void *f[2] = {nullptr, nullptr};
+    void *g[2] = {nullptr, nullptr};
+    int fcur = 0, gcur = 0;  // buffer holding the current state (read by the next step)
+    void *link = nullptr;
+    int link32 = 0;
+    uint8_t *cls_cur = nullptr, *cls_tmp = nullptr;
+    float *fld_rho = nullptr, *fld_u = nullptr, *fld_c = nullptr;
+    double *partials = nullptr;
+    double *results_d = nullptr, *results_h = nullptr;
+    unsigned long long *counts_d = nullptr, *counts_h = nullptr;
+    double *staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaEvent_t done = nullptr;
+    float c_ref = 1.0f;
+    int grid = 1, block = mfc::DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
+
+    std::vector<mfc::GraphEntry> graphs;
+    long flow_open = 0, ade_open = 0;
+    double last_current = 0.0;
+    size_t bytes = 0;
+    std::string err;
+    mfc_status sticky = MFC_OK;
+};
+
+namespace mfc {
+
+// Create a lattice like mfc_create_lattice; with a pool, every device buffer is allocated from
+// it on the lattice's stream (desc->stream must then be given) and freed back to it.
+mfc_status lattice_create(const mfc_lattice_desc *desc, const mfc_params *params, cudaMemPool_t pool,
+                          mfc_lattice **out, std::string *why);
+// The checks mfc_create_lattice applies to a descriptor and parameters.
+mfc_status validate_lattice(const mfc_lattice_desc *desc, const mfc_params *params, std::string *why);
+// Step arguments of the lattice for one step of `kind` in `mode` from its current buffers.
+void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h);
+// Seconds on the steady clock (the clock of mfc_clock and of the batch time stamps).
+double now_s();
+
+}  // namespace mfc

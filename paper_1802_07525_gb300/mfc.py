@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libmfc.so")
 
 MFC_OK, MFC_ERR_ARG, MFC_ERR_OOM, MFC_ERR_OOM_BUDGET, MFC_ERR_CUDA = 0, 1, 2, 3, 4
-MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_TIMEOUT, MFC_ERR_STATE = 5, 6, 7, 8
+MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_TIMEOUT, MFC_ERR_STATE, MFC_PENDING = 5, 6, 7, 8, 9
 MFC_BC_WALL, MFC_BC_PERIODIC, MFC_BC_INOUT = 0, 1, 2
 MFC_FP32, MFC_FP16_DEV = 0, 1
 MFC_SEQUENTIAL, MFC_CONCURRENT = 0, 1
@@ -65,6 +65,29 @@ class Launch(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("block", ctypes.c_int),
+                ("max_instances", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("result", SolveResult), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("running", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("blocks", ctypes.c_longlong), ("instance_steps", ctypes.c_longlong),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("check_every", ctypes.c_int),
+                ("block", ctypes.c_int), ("grid", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MfcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_string(status)} ({status}): {msg}")
@@ -96,6 +119,20 @@ _SIGS = {
     "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_field_sums_noalloc": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_double, _vp, _vp]),
+    "mfc_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchOpts), ctypes.POINTER(_vp)]),
+    "mfc_batch_destroy": (ctypes.c_int, [_vp]),
+    "mfc_batch_submit": (ctypes.c_int, [_vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Params),
+                                        ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(SolveOpts),
+                                        _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "mfc_batch_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(BatchResult)]),
+    "mfc_batch_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_double,
+                                      ctypes.POINTER(BatchResult)]),
+    "mfc_batch_run": (ctypes.c_int, [_vp]),
+    "mfc_batch_start": (ctypes.c_int, [_vp]),
+    "mfc_batch_stop": (ctypes.c_int, [_vp]),
+    "mfc_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(BatchStats)]),
+    "mfc_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "mfc_clock": (ctypes.c_double, []),
     "mfc_active_nodes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_long),
                                         ctypes.POINTER(ctypes.c_long)]),
     "mfc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -282,3 +319,102 @@ class Lattice:
         b = ctypes.c_size_t()
         self._check(self._L.mfc_device_bytes(self.handle, ctypes.byref(b)))
         return int(b.value)
+
+
+class Batch:
+    """Many steady solves sharing the GPU with continuous batching (``mfc_batch_*``).
+
+    ``submit`` queues a solve and returns a ticket; the engine runs on the caller's thread
+    (``run``) or on a library thread (``start`` / ``stop``).  ``poll`` and ``wait`` return
+    ``None`` while the request is pending, else a dict with the solve result, the time stamps
+    (``mfc_clock`` seconds) and, when asked for, the fields ``rho``, ``u``, ``c``."""
+
+    def __init__(self, *, budget_bytes=0, precision=MFC_FP32, check_every=0, block=0,
+                 max_instances=0, stream=None):
+        self._L = lib()
+        o = BatchOpts(int(budget_bytes), precision, int(check_every), int(block),
+                      int(max_instances), stream)
+        h = ctypes.c_void_p()
+        st = self._L.mfc_batch_create(ctypes.byref(o), ctypes.byref(h))
+        if st != MFC_OK:
+            raise MfcError(st, "mfc_batch_create")
+        self.handle = h
+        self.precision = precision
+        self._pending = {}  # ticket -> (shape, host buffers kept alive until the solve ends)
+
+    def submit(self, shape, node_class, *, bc=None, tol_flow=1e-7, tol_ade=1e-7,
+               max_steps=100000, timeout_s=0.0, fields=True, **params) -> int:
+        shape = tuple(int(v) for v in shape)
+        n = int(np.prod(shape))
+        dim = len(shape)
+        cls = np.ascontiguousarray(np.asarray(node_class, dtype=np.uint8).reshape(-1))
+        if cls.size != n:
+            raise ValueError("node_class must hold one class per node")
+        bufs = (np.empty(n), np.empty((dim, n)), np.empty(n)) if fields else (None, None, None)
+        desc = make_desc(shape, bc, self.precision)
+        prm = make_params(**params)
+        opts = SolveOpts(tol_flow, tol_ade, int(max_steps), 0, MFC_CONCURRENT, timeout_s)
+        t = ctypes.c_longlong(0)
+        st = self._L.mfc_batch_submit(self.handle, ctypes.byref(desc), ctypes.byref(prm),
+                                      _ptr(cls, ctypes.c_uint8), ctypes.byref(opts),
+                                      _ptr(bufs[0]), _ptr(bufs[1]), _ptr(bufs[2]), ctypes.byref(t))
+        if st != MFC_OK:
+            raise MfcError(st, "mfc_batch_submit")
+        self._pending[t.value] = (shape, bufs)
+        return t.value
+
+    def _result(self, ticket, st, r):
+        if st == MFC_PENDING:
+            return None
+        if st == MFC_ERR_ARG and ticket not in self._pending:
+            raise MfcError(st, f"unknown ticket {ticket}")
+        _, bufs = self._pending.pop(ticket)
+        out = r.result.as_dict()
+        out.update(t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done, ticket=ticket)
+        if bufs[0] is not None and st not in (MFC_ERR_CUDA,):
+            out.update(rho=bufs[0], u=bufs[1], c=bufs[2])
+        return out
+
+    def poll(self, ticket):
+        r = BatchResult()
+        st = self._L.mfc_batch_poll(self.handle, ticket, ctypes.byref(r))
+        return self._result(ticket, st, r)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = BatchResult()
+        st = self._L.mfc_batch_wait(self.handle, ticket, float(timeout_s), ctypes.byref(r))
+        return self._result(ticket, st, r)
+
+    def run(self):
+        st = self._L.mfc_batch_run(self.handle)
+        if st != MFC_OK:
+            raise MfcError(st, self._L.mfc_batch_last_error(self.handle).decode())
+
+    def start(self):
+        st = self._L.mfc_batch_start(self.handle)
+        if st != MFC_OK:
+            raise MfcError(st, "mfc_batch_start")
+
+    def stop(self):
+        self._L.mfc_batch_stop(self.handle)
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        self._L.mfc_batch_get_stats(self.handle, ctypes.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            self._L.mfc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def clock() -> float:
+    """Seconds on the library's monotonic clock (the clock of the batch time stamps)."""
+    return float(lib().mfc_clock())
