@@ -1,23 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of the coupled flow + substrate-transport lattice Boltzmann hot path on GB300.
 
-Workload: the 2048x1024 porous anode (random overlapping discs of radius 6, porosity 0.7 in the
-middle half of the channel, seeded), D2Q9 flow + D2Q5 transport, FP32 storage and arithmetic
-(FP64 reductions).  One step is one fused update of every node of both lattices; steps run in
-CUDA-graph blocks of K (default 200) that end with the residual/current reduction and the
-host-side convergence decision, exactly as a steady solve runs them (tolerance 0, so every
-block is taken).  The working set (2 x 14 planes x 4 B x 2.1 M nodes = 235 MB of populations)
-is larger than the 129 MB L2, so no explicit flush is needed between steps.
+Headline workload: the 2048x1024 porous anode (random overlapping discs of radius 6, porosity
+0.7 in the middle half of the channel, seeded), D2Q9 flow + D2Q5 transport, FP32 storage and
+arithmetic (FP64 reductions).  One step is one fused update of every node of both lattices;
+steps run in CUDA-graph blocks of K (default 200) that end with the residual/current reduction
+and the host-side convergence decision, exactly as a steady solve runs them (tolerance 0, so
+every block is taken).  The working set (2 x 14 planes x 4 B x 2.1 M nodes = 235 MB of
+populations) is larger than the 129 MB L2, so no explicit flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Further legs on one GPU (rank 0 of a 1-GPU run), each reported in the same JSON line:
+  variants  - the FP16-storage 2-D step and the 3-D 256x128x128 electrode (FP32, FP16):
+              MLUPS and fraction of the HBM roofline;
+  accuracy  - FP32 and FP16 results against the FP64 oracle (populations after a fixed number
+              of steps, steady fields and current), the oracle running in spawned processes
+              while the GPU legs run;
+  batch     - 64 uneven 2-D instances solved to 1e-7 by the batch engine against the same
+              solves one at a time (solves/s at equal accuracy);
+  serve     - a Poisson stream of 2-D/3-D steady-solve requests through the batch engine's
+              thread: capacity at the offered rate of 200/s, then p50/p99 latency at 0.8x the
+              measured capacity.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--legs ...]
 
 Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) are independent replicas, one lattice
-per GPU, each with its own seed (weak scaling, no data-path collective).
+per GPU, each with its own seed (weak scaling, no data-path collective); they run the headline
+leg only.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -30,6 +44,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coupled flow+ADE MLUPS & % of HBM roofline; served solves/s with p50/p99 latency"
 WORKLOAD = "anode_2d_2048x1024_fused_d2q9_d2q5"
+ALL_LEGS = "main,variants,accuracy,batch,serve"
 
 
 def parse():
@@ -45,6 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1000,
                     help="lattice updates per end-to-end step (upload, solve block, read back)")
+    ap.add_argument("--legs", default=ALL_LEGS,
+                    help="comma-separated subset of " + ALL_LEGS)
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--serve-count", type=int, default=24, help="requests per serving phase")
     return ap.parse_args()
 
 
@@ -121,10 +140,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def wkw(w):
+    return dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
+
+
+# ---- oracle side (CPU) -----------------------------------------------------------------------
+
 def cpu_baseline(w, seconds_target=10.0):
     """The FP64 oracle as it stands, one thread, on a bounded sample: fused steps of the full
     2048x1024 anode from rest, as many as fit about ten seconds."""
-    import numpy as np  # noqa: F401
     import oracle
     o = oracle.Oracle(w.shape, w.cls, tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in,
                       k_sink=w.k_sink)
@@ -140,19 +164,49 @@ def cpu_baseline(w, seconds_target=10.0):
                       f"from rest, FP64 C oracle, 1 thread ({dt:.1f} s)"}
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of the kernel from the committed ncu summary, if it was taken
-    on the kernel code that is built now (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
-    with open(p) as fh:
-        d = json.load(fh)
-    from paper_1802_07525_gb300 import build
-    rec = d.get(kernel)
-    if not rec or rec.get("kernel_digest") != build.kernel_digest(rec["translation_unit"]):
-        return None
-    return rec.get("dram_bytes_per_launch_full")
+# The accuracy cases: (name, workload factory and arguments, steps or "steady").
+ACC_CASES = [
+    ("2d_256x128_1000_steps", ("anode_2d", (256, 128), {"seed": 2}), 1000),
+    ("2d_64x32_steady", ("anode_2d", (64, 32), {"seed": 7}), "steady"),
+    ("3d_48x32x32_200_steps", ("electrode_3d", (48, 32, 32), {"seed": 3}), 200),
+    ("3d_16x16x24_steady", ("electrode_3d", (16, 16, 24), {"seed": 9}), "steady"),
+]
+ACC_K = 100
+
+
+def _acc_workload(spec):
+    import mfc_inputs as mi
+    fn, shape, kw = spec
+    return getattr(mi, fn)(*shape, **kw)
+
+
+def oracle_case(case):
+    """One accuracy reference on the FP64 oracle (run in a spawned process)."""
+    import oracle
+    name, spec, steps = case
+    w = _acc_workload(spec)
+    o = oracle.Oracle(w.shape, w.cls, **wkw(w))
+    t0 = time.perf_counter()
+    if steps == "steady":
+        r = o.solve_steady(mode=oracle.CONCURRENT, tol_flow=w.tol, tol_ade=w.tol,
+                           max_steps=w.max_steps, check_every=ACC_K)
+        extra = {"steps": int(r.steps_flow), "current": float(r.current),
+                 "converged": int(r.converged)}
+    else:
+        o.step_coupled(steps)
+        extra = {"steps": steps}
+    extra["oracle_s"] = time.perf_counter() - t0
+    return name, {"f": o.f.copy(), "g": o.g.copy(), "u": o.u.copy(), "c": o.conc.copy(), **extra}
+
+
+def start_oracle_pool():
+    """Spawned worker processes (started before the first GPU call) computing the references."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    oracle.build()  # once, before the workers import it
+    ex = cf.ProcessPoolExecutor(max_workers=len(ACC_CASES), mp_context=mp.get_context("spawn"))
+    return ex, [ex.submit(oracle_case, c) for c in ACC_CASES]
 
 
 def run_reference(args, rank, world):
@@ -160,14 +214,12 @@ def run_reference(args, rank, world):
     workload's rows, sized so that the whole run ends within a few minutes."""
     if rank != 0:
         return
-    import numpy as np
     import mfc_inputs as mi
     import oracle
     w = mi.anode_2d(args.nx, args.ny)
     total = args.steps + args.warmup
     budget = 150.0 / max(total, 1)
-    # calibrate on a 16-row slab
-    rows = 16
+    rows = 16  # calibrate on a 16-row slab
 
     def slab(r):
         y0 = w.shape[1] // 2 - r // 2
@@ -201,15 +253,229 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def traffic_record(kernel):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if it was taken
+    on the kernel code that is built now (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    from paper_1802_07525_gb300 import build
+    rec = d.get(kernel)
+    if not rec or "translation_unit" not in rec or \
+            rec.get("kernel_digest") != build.kernel_digest(rec["translation_unit"]):
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+# ---- GPU legs --------------------------------------------------------------------------------
+
+def time_plain_steps(P, lat, stream, M=400):
+    """Average duration of the plain fused step kernel: M launches on the lattice stream,
+    bracketed by CUDA events on that stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.step_coupled(20)
+    e0.record(stream)
+    lat.step_coupled(M)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / M
+
+
+def step_bytes(dim, prec_bytes, flow_open, ade_open):
+    """Algorithmic bytes of one fused step: every population of every open node read once and
+    written once."""
+    qf, qa = (9, 5) if dim == 2 else (19, 7)
+    return 2 * prec_bytes * (qf * flow_open + qa * ade_open)
+
+
+def leg_variants(P, peak):
+    """FP16-storage 2-D step and the 3-D electrode in FP32 and FP16: MLUPS over graph blocks
+    and the plain kernel's fraction of the HBM roofline."""
+    import torch
+    import mfc_inputs as mi
+    out = {}
+    cases = [("2d_2048x1024_fp16", mi.anode_2d(), P.MFC_FP16_DEV, 20000),
+             ("3d_256x128x128_fp32", mi.electrode_3d(), P.MFC_FP32, 5000),
+             ("3d_256x128x128_fp16", mi.electrode_3d(), P.MFC_FP16_DEV, 5000)]
+    for name, w, prec, steps in cases:
+        stream = torch.cuda.Stream()
+        lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, **wkw(w))
+        lat.set_geometry(w.cls)
+        fo, ao = lat.active_nodes()
+        lat.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=1000,
+                         check_every=200)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=steps,
+                         check_every=200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kern_ms = time_plain_steps(P, lat, stream)
+        sb = 2 if prec == P.MFC_FP16_DEV else 4
+        byt = step_bytes(w.dim, sb, fo, ao)
+        ach = byt / (kern_ms * 1e-3) / 1e9
+        out[name] = {"mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": byt,
+                     "achieved_gbs": ach, "roofline_frac": ach / peak,
+                     "bytes_per_node": byt / w.nodes}
+        lat.close()
+    return out
+
+
+def gpu_case(P, case, prec):
+    name, spec, steps = case
+    w = _acc_workload(spec)
+    g = P.Lattice(w.shape, precision=prec, **wkw(w))
+    g.set_geometry(w.cls)
+    res = {}
+    if steps == "steady":
+        r = g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=w.tol, tol_ade=w.tol,
+                           max_steps=w.max_steps, check_every=ACC_K)
+        res.update(steps=int(r.steps_flow), current=float(r.current), status=int(r.status))
+    else:
+        g.step_coupled(steps)
+    _, u, c, _ = g.read_fields()
+    res.update(f=g.read_populations(P.MFC_POP_FLOW), g=g.read_populations(P.MFC_POP_ADE), u=u, c=c)
+    g.close()
+    return res
+
+
+def leg_accuracy(P, futures):
+    """FP32 and FP16 results against the FP64 oracle references."""
+    import numpy as np
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    refs = dict(f.result() for f in futures)
+    out = {}
+    for prec_name, prec in (("fp32", P.MFC_FP32), ("fp16", P.MFC_FP16_DEV)):
+        d = {}
+        for case in ACC_CASES:
+            name, _, steps = case
+            ref = refs[name]
+            got = gpu_case(P, case, prec)
+            e = {"u_rel_l2": rel(got["u"], ref["u"]), "c_rel_l2": rel(got["c"], ref["c"])}
+            if steps == "steady":
+                e.update(current_rel=abs(got["current"] - ref["current"]) / abs(ref["current"]),
+                         steps=got["steps"], oracle_steps=ref["steps"], status=got["status"])
+            else:
+                e.update(pop_flow_maxabs=float(np.abs(got["f"] - ref["f"]).max()),
+                         pop_ade_maxabs=float(np.abs(got["g"] - ref["g"]).max()), steps=steps)
+            d[name] = e
+        out[prec_name] = d
+    out["oracle_seconds"] = {k: v["oracle_s"] for k, v in refs.items()}
+    out["check_every"] = ACC_K
+    return out
+
+
+def leg_batch(P, count):
+    """The uneven batch (64 instances of 256..1024 x 128..512, porosity, tau and inlet speed
+    drawn per instance) solved to 1e-7 by the batch engine, then the same solves one at a time
+    with the same K; wall-clock solves/s of both and the agreement of their results."""
+    import numpy as np
+    import mfc_inputs as mi
+    works = mi.batch_instances(count)
+    b = P.Batch()
+    t0 = time.perf_counter()
+    tickets = [b.submit(w.shape, w.cls, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        **wkw(w)) for w in works]
+    b.run()
+    tb = time.perf_counter() - t0
+    rb = [b.poll(t) for t in tickets]
+    st = b.stats()
+    b.close()
+    K = st["check_every"]
+    t0 = time.perf_counter()
+    rs = []
+    for w in works:
+        g = P.Lattice(w.shape, **wkw(w))
+        g.set_geometry(w.cls)
+        r = g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=w.tol, tol_ade=w.tol,
+                           max_steps=w.max_steps, check_every=K)
+        _, u, c, _ = g.read_fields()
+        rs.append((r, u, c))
+        g.close()
+    ts = time.perf_counter() - t0
+    du = max(float(np.linalg.norm(x["u"] - u) / np.linalg.norm(u)) for x, (_, u, _) in zip(rb, rs))
+    dc = max(float(np.linalg.norm(x["c"] - c) / np.linalg.norm(c)) for x, (_, _, c) in zip(rb, rs))
+    upd = sum(x["steps_flow"] * w.nodes for x, w in zip(rb, works))
+    return {"instances": count, "nodes": int(sum(w.nodes for w in works)), "tol": works[0].tol,
+            "batched_s": tb, "batched_solves_per_s": count / tb,
+            "one_at_a_time_s": ts, "one_at_a_time_solves_per_s": count / ts,
+            "speedup": ts / tb, "check_every": K, "block": st["block"], "grid": st["grid"],
+            "converged": sum(x["status"] == P.MFC_OK for x in rb),
+            "same_stop_step": sum(x["steps_flow"] == r.steps_flow for x, (r, _, _) in zip(rb, rs)),
+            "max_rel_l2_u_batch_vs_alone": du, "max_rel_l2_c_batch_vs_alone": dc,
+            "batched_mlups": upd / tb / 1e6, "mean_steps": upd / sum(w.nodes for w in works)}
+
+
+def serve_phase(P, reqs, works, rate_scale):
+    """Submit each request at its arrival time (scaled) to the batch engine's thread; return
+    per-request latency (submission to result) and the achieved solves/s."""
+    b = P.Batch(budget_bytes=150 * 10 ** 9)
+    b.start()
+    t0 = P.clock()
+    tickets = []
+    for r, w in zip(reqs, works):
+        delay = t0 + r.arrival_s * rate_scale - P.clock()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(b.submit(w.shape, w.cls, tol_flow=w.tol, tol_ade=w.tol,
+                                max_steps=w.max_steps, **wkw(w)))
+    res = [b.wait(t, timeout_s=600.0) for t in tickets]
+    b.stop()
+    st = b.stats()
+    b.close()
+    lat = sorted(x["t_done"] - x["t_submit"] for x in res)
+    span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+    first, last = min(x["t_submit"] for x in res), max(x["t_submit"] for x in res)
+    return {"requests": len(res), "solves_per_s": len(res) / span, "span_s": span,
+            "offered_per_s": (len(res) - 1) / max(last - first, 1e-9),
+            "p50_s": lat[len(lat) // 2],
+            "p99_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "max_s": lat[-1], "converged": sum(x["status"] == P.MFC_OK for x in res),
+            "at_cap": sum(x["status"] == P.MFC_NOT_CONVERGED for x in res),
+            "check_every": st["check_every"], "block": st["block"],
+            "peak_bytes": st["bytes_peak"]}
+
+
+def leg_serve(P, count):
+    """Serving: Poisson arrivals of 2-D (512..2048 x 256..1024) and 3-D (64^3..192x96x96)
+    steady-solve requests (tol 1e-7, cap 1e5 steps), 150 GB admission budget.  Phase 1 offers
+    the stream at 200/s (capacity); phase 2 offers a second stream at 0.8x that capacity."""
+    import mfc_inputs as mi
+    reqs1 = mi.serving_stream(count, 200.0, seed=5)
+    works1 = [r.workload() for r in reqs1]
+    p1 = serve_phase(P, reqs1, works1, 1.0)
+    rate2 = 0.8 * p1["solves_per_s"]
+    reqs2 = mi.serving_stream(count, 200.0, seed=6)
+    works2 = [r.workload() for r in reqs2]
+    p2 = serve_phase(P, reqs2, works2, 200.0 / rate2)
+    return {"offered_200_per_s": p1, "offered_0.8x_capacity": p2,
+            "mix": "70% 2-D, 30% 3-D by request", "requests_per_phase": count}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    legs = set(args.legs.split(","))
     if world > 1:
         # one GPU per rank: the library and torch both see it as device 0
         os.environ["CUDA_VISIBLE_DEVICES"] = str(local)
+        legs &= {"main"}
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+
+    pool = futures = None
+    if "accuracy" in legs and rank == 0:
+        pool, futures = start_oracle_pool()  # before the first GPU call
 
     import numpy as np
     import torch
@@ -228,8 +494,7 @@ def main():
     w = mi.anode_2d(args.nx, args.ny, seed=2 + rank)
     prec = P.MFC_FP16_DEV if args.precision == "fp16" else P.MFC_FP32
     stream = torch.cuda.Stream()
-    lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, tau=w.tau,
-                    tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
+    lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, **wkw(w))
     lat.set_geometry(w.cls)
     flow_open, ade_open = lat.active_nodes()
     K = args.check_every
@@ -269,16 +534,9 @@ def main():
     value = total_nodes * args.steps / (ms * 1e-3) / 1e6
 
     # dominant kernel: the plain fused step, timed alone on the same stream
-    M = 400
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat.step_coupled(20)
-    e0.record(stream)
-    lat.step_coupled(M)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    kern_ms = e0.elapsed_time(e1) / M
+    kern_ms = time_plain_steps(P, lat, stream)
     sb = 2 if prec == P.MFC_FP16_DEV else 4
-    bytes_per_launch = 2 * sb * (9 * flow_open + 5 * ade_open)
+    bytes_per_launch = step_bytes(2, sb, flow_open, ade_open)
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
     kname = "lbm_step_kernel<2,%s,true,true,0>" % ("half" if sb == 2 else "float")
@@ -323,13 +581,30 @@ def main():
         e2e_s = float(t.item())
     e2e_value = total_nodes * args.e2e_steps * n_e2e / e2e_s / 1e6
     assert np.isfinite(c_h.numpy()).all()
+    lat.close()
+
+    extra = {}
+    leg_s = {}
+    if rank == 0 and world == 1:
+        for name, fn in (("variants", lambda: leg_variants(P, peak)),
+                         ("accuracy", lambda: leg_accuracy(P, futures)),
+                         ("batch", lambda: leg_batch(P, args.batch_count)),
+                         ("serve", lambda: leg_serve(P, args.serve_count))):
+            if name in legs:
+                t0 = time.perf_counter()
+                extra[name] = fn()
+                leg_s[name] = time.perf_counter() - t0
+    if pool:
+        pool.shutdown()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
     if rank == 0:
-        launches = args.steps + (args.steps + K - 1) // K
+        nblocks = (args.steps + K - 1) // K
+        # per block: K step kernels and the two sum kernels
+        launches = args.steps + 2 * nblocks
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -354,8 +629,15 @@ def main():
             "clocks": clocks.summary(),
             "final": {"res_flow": res.res_flow, "res_ade": res.res_ade, "current": res.current},
         }
+        if "serve" in extra:
+            s = extra["serve"]
+            line["serving"] = {"solves_per_s": s["offered_200_per_s"]["solves_per_s"],
+                               "p50_s": s["offered_0.8x_capacity"]["p50_s"],
+                               "p99_s": s["offered_0.8x_capacity"]["p99_s"], **extra.pop("serve")}
+        line.update(extra)
+        if leg_s:
+            line["leg_seconds"] = leg_s
         print(json.dumps(line), flush=True)
-    lat.close()
     if pg:
         pg.destroy_process_group()
 
