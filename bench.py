@@ -19,7 +19,10 @@ Further legs on one GPU (rank 0 of a 1-GPU run), each reported in the same JSON 
               solves one at a time (solves/s at equal accuracy);
   serve     - a Poisson stream of 2-D/3-D steady-solve requests through the batch engine's
               thread: capacity at the offered rate of 200/s, then p50/p99 latency at 0.8x the
-              measured capacity.
+              measured capacity;
+  biofilm   - (only when asked for: it takes minutes) the 2048x1024 anode through 50 biofilm
+              cycles: each cycle solves flow and transport to steady state (1e-7, at most 1e5
+              steps), then grows biofilm by the seeded rule and warm-starts the next.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--legs ...]
 
@@ -45,6 +48,7 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled flow+ADE MLUPS & % of HBM roofline; served solves/s with p50/p99 latency"
 WORKLOAD = "anode_2d_2048x1024_fused_d2q9_d2q5"
 ALL_LEGS = "main,variants,accuracy,batch,serve"
+EXTRA_LEGS = "biofilm"
 
 
 def parse():
@@ -61,7 +65,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1000,
                     help="lattice updates per end-to-end step (upload, solve block, read back)")
     ap.add_argument("--legs", default=ALL_LEGS,
-                    help="comma-separated subset of " + ALL_LEGS)
+                    help="comma-separated subset of " + ALL_LEGS + "," + EXTRA_LEGS)
+    ap.add_argument("--biofilm-cycles", type=int, default=50)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=24, help="requests per serving phase")
     return ap.parse_args()
@@ -297,7 +302,8 @@ def leg_variants(P, peak):
     import torch
     import mfc_inputs as mi
     out = {}
-    cases = [("2d_2048x1024_fp16", mi.anode_2d(), P.MFC_FP16_DEV, 20000),
+    # the FP16 2-D case runs on 4096x1024: its 2048x1024 working set (118 MB) would fit the L2
+    cases = [("2d_4096x1024_fp16", mi.anode_2d(4096, 1024), P.MFC_FP16_DEV, 10000),
              ("3d_256x128x128_fp32", mi.electrode_3d(), P.MFC_FP32, 5000),
              ("3d_256x128x128_fp16", mi.electrode_3d(), P.MFC_FP16_DEV, 5000)]
     for name, w, prec, steps in cases:
@@ -461,6 +467,34 @@ def leg_serve(P, count):
             "mix": "70% 2-D, 30% 3-D by request", "requests_per_phase": count}
 
 
+def leg_biofilm(P, cycles):
+    """The biofilm-cycle workload: steady solve, growth, warm restart, `cycles` times."""
+    import torch
+    import mfc_inputs as mi
+    w = mi.anode_2d()
+    stream = torch.cuda.Stream()
+    lat = P.Lattice(w.shape, stream=stream.cuda_stream, **wkw(w))
+    lat.set_geometry(w.cls)
+    per = []
+    t0 = time.perf_counter()
+    steps = 0
+    for cyc in range(cycles):
+        r = lat.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=w.tol, tol_ade=w.tol,
+                             max_steps=w.max_steps, check_every=200)
+        n = lat.biofilm_grow(seed=2, cycle=cyc, prob=0.05, c_thresh=0.5)
+        steps += r.steps_flow
+        per.append({"steps": int(r.steps_flow), "status": int(r.status), "current": r.current,
+                    "res_flow": r.res_flow, "res_ade": r.res_ade, "converted": n})
+    dt = time.perf_counter() - t0
+    lat.close()
+    return {"cycles": cycles, "seconds": dt, "steps": steps,
+            "mlups": w.nodes * steps / dt / 1e6,
+            "converged": sum(c["status"] == P.MFC_OK for c in per),
+            "converted_total": sum(c["converted"] for c in per),
+            "current_first": per[0]["current"], "current_last": per[-1]["current"],
+            "per_cycle": per}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -589,7 +623,8 @@ def main():
         for name, fn in (("variants", lambda: leg_variants(P, peak)),
                          ("accuracy", lambda: leg_accuracy(P, futures)),
                          ("batch", lambda: leg_batch(P, args.batch_count)),
-                         ("serve", lambda: leg_serve(P, args.serve_count))):
+                         ("serve", lambda: leg_serve(P, args.serve_count)),
+                         ("biofilm", lambda: leg_biofilm(P, args.biofilm_cycles))):
             if name in legs:
                 t0 = time.perf_counter()
                 extra[name] = fn()
