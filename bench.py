@@ -47,6 +47,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coupled flow+ADE MLUPS & % of HBM roofline; served solves/s with p50/p99 latency"
 WORKLOAD = "anode_2d_2048x1024_fused_d2q9_d2q5"
+WORKLOADS = {"anode2d": WORKLOAD, "electrode3d": "electrode_3d_256x128x128_fused_d3q19_d3q7"}
 ALL_LEGS = "main,variants,accuracy,batch,serve"
 EXTRA_LEGS = "biofilm"
 
@@ -67,9 +68,30 @@ def parse():
     ap.add_argument("--legs", default=ALL_LEGS,
                     help="comma-separated subset of " + ALL_LEGS + "," + EXTRA_LEGS)
     ap.add_argument("--biofilm-cycles", type=int, default=50)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="anode2d",
+                    help="lattice of the headline leg (anode2d: --nx x --ny anode; electrode3d: "
+                         "the 256x128x128 electrode)")
+    ap.add_argument("--batch-max-steps", type=int, default=0,
+                    help="step cap of the batch leg's solves (0: the workload's own cap)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=24, help="requests per serving phase")
     return ap.parse_args()
+
+
+def max_over_ranks(x, pg, device):
+    """The largest value of x over the ranks of the process group (x itself without one)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank, world, updates, seconds):
+    """Whole-job lattice updates per second (millions): every rank's nodes, the slowest rank's
+    time (weak scaling: each rank advances its own lattice)."""
+    return nodes_per_rank * world * updates / seconds / 1e6
 
 
 def dist_env():
@@ -380,7 +402,7 @@ def leg_accuracy(P, futures):
     return out
 
 
-def leg_batch(P, count):
+def leg_batch(P, count, max_steps=0):
     """The uneven batch (64 instances of 256..1024 x 128..512, porosity, tau and inlet speed
     drawn per instance) solved to 1e-7 by the batch engine, then the same solves one at a time
     with the same K; wall-clock solves/s of both and the agreement of their results."""
@@ -389,8 +411,8 @@ def leg_batch(P, count):
     works = mi.batch_instances(count)
     b = P.Batch()
     t0 = time.perf_counter()
-    tickets = [b.submit(w.shape, w.cls, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
-                        **wkw(w)) for w in works]
+    tickets = [b.submit(w.shape, w.cls, tol_flow=w.tol, tol_ade=w.tol,
+                        max_steps=max_steps or w.max_steps, **wkw(w)) for w in works]
     b.run()
     tb = time.perf_counter() - t0
     rb = [b.poll(t) for t in tickets]
@@ -403,7 +425,7 @@ def leg_batch(P, count):
         g = P.Lattice(w.shape, **wkw(w))
         g.set_geometry(w.cls)
         r = g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=w.tol, tol_ade=w.tol,
-                           max_steps=w.max_steps, check_every=K)
+                           max_steps=max_steps or w.max_steps, check_every=K)
         _, u, c, _ = g.read_fields()
         rs.append((r, u, c))
         g.close()
@@ -525,7 +547,10 @@ def main():
         dist.init_process_group("nccl", rank=rank, world_size=world)
         pg = dist
 
-    w = mi.anode_2d(args.nx, args.ny, seed=2 + rank)
+    if args.workload == "electrode3d":
+        w = mi.electrode_3d(seed=3 + rank)
+    else:
+        w = mi.anode_2d(args.nx, args.ny, seed=2 + rank)
     prec = P.MFC_FP16_DEV if args.precision == "fp16" else P.MFC_FP32
     stream = torch.cuda.Stream()
     lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, **wkw(w))
@@ -559,21 +584,18 @@ def main():
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    total_nodes = w.nodes * world
-    value = total_nodes * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
+    value = aggregate_mlups(w.nodes, world, args.steps, ms * 1e-3)
 
     # dominant kernel: the plain fused step, timed alone on the same stream
     kern_ms = time_plain_steps(P, lat, stream)
     sb = 2 if prec == P.MFC_FP16_DEV else 4
-    bytes_per_launch = step_bytes(2, sb, flow_open, ade_open)
+    qf, qa = (9, 5) if w.dim == 2 else (19, 7)
+    working_set = 2 * sb * (qf + qa) * w.nodes
+    bytes_per_launch = step_bytes(w.dim, sb, flow_open, ade_open)
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
-    kname = "lbm_step_kernel<2,%s,true,true,0>" % ("half" if sb == 2 else "float")
+    kname = "lbm_step_kernel<%d,%s,true,true,0>" % (w.dim, "half" if sb == 2 else "float")
     traffic = traffic_record(kname)
 
     # end to end through the public API with host buffers: upload classes from pinned memory,
@@ -581,7 +603,7 @@ def main():
     n_e2e = 3
     cls_h = torch.from_numpy(w.cls).pin_memory()
     rho_h = torch.empty(w.nodes, dtype=torch.float64).pin_memory()
-    u_h = torch.empty(2 * w.nodes, dtype=torch.float64).pin_memory()
+    u_h = torch.empty(w.dim * w.nodes, dtype=torch.float64).pin_memory()
     c_h = torch.empty(w.nodes, dtype=torch.float64).pin_memory()
     cur_h = torch.empty(1, dtype=torch.float64).pin_memory()
     import ctypes
@@ -608,12 +630,8 @@ def main():
     for _ in range(n_e2e):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = total_nodes * args.e2e_steps * n_e2e / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+    e2e_value = aggregate_mlups(w.nodes, world, args.e2e_steps * n_e2e, e2e_s)
     assert np.isfinite(c_h.numpy()).all()
     lat.close()
 
@@ -622,7 +640,7 @@ def main():
     if rank == 0 and world == 1:
         for name, fn in (("variants", lambda: leg_variants(P, peak)),
                          ("accuracy", lambda: leg_accuracy(P, futures)),
-                         ("batch", lambda: leg_batch(P, args.batch_count)),
+                         ("batch", lambda: leg_batch(P, args.batch_count, args.batch_max_steps)),
                          ("serve", lambda: leg_serve(P, args.serve_count)),
                          ("biofilm", lambda: leg_biofilm(P, args.biofilm_cycles))):
             if name in legs:
@@ -633,7 +651,7 @@ def main():
         pool.shutdown()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.dim == 2:
         cpu = cpu_baseline(w)
 
     if rank == 0:
@@ -645,10 +663,12 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if sb == 4 else "f16-storage/f32-math", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": args.nx, "ny": args.ny,
+            "config": {"workload": WORKLOADS[args.workload], "shape": list(w.shape),
                        "nodes_per_gpu": w.nodes, "flow_open": flow_open, "ade_open": ade_open,
                        "check_every": K, "parallelism": f"replicas{world}",
-                       "l2": "working set 235 MB > 129 MB L2, no flush",
+                       "l2": f"populations {working_set / 1e6:.0f} MB (both buffers) "
+                             f"{'>' if working_set > 129e6 else '<='} 129 MB L2"
+                             f"{', no flush' if working_set > 129e6 else ' (L2-resident: not a valid HBM number)'}",
                        "mflups_flow_open": flow_open * world * args.steps / (ms * 1e-3) / 1e6},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -658,7 +678,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": int(w.nodes),
-                    "d2h_bytes_per_step": int(w.nodes * 8 * 4 + 8),
+                    "d2h_bytes_per_step": int(w.nodes * 8 * (2 + w.dim) + 8),
                     "updates_per_step": args.e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
