@@ -430,14 +430,20 @@ def leg_batch(P, count, max_steps=0):
         rs.append((r, u, c))
         g.close()
     ts = time.perf_counter() - t0
-    du = max(float(np.linalg.norm(x["u"] - u) / np.linalg.norm(u)) for x, (_, u, _) in zip(rb, rs))
-    dc = max(float(np.linalg.norm(x["c"] - c) / np.linalg.norm(c)) for x, (_, _, c) in zip(rb, rs))
+    # field agreement over the solves that ended with finite fields in both arms
+    fin = [(x, y) for x, y in zip(rb, rs)
+           if x["status"] != P.MFC_ERR_NONFINITE and y[0].status != P.MFC_ERR_NONFINITE]
+    du = max(float(np.linalg.norm(x["u"] - u) / np.linalg.norm(u)) for x, (_, u, _) in fin)
+    dc = max(float(np.linalg.norm(x["c"] - c) / np.linalg.norm(c)) for x, (_, _, c) in fin)
     upd = sum(x["steps_flow"] * w.nodes for x, w in zip(rb, works))
     return {"instances": count, "nodes": int(sum(w.nodes for w in works)), "tol": works[0].tol,
             "batched_s": tb, "batched_solves_per_s": count / tb,
             "one_at_a_time_s": ts, "one_at_a_time_solves_per_s": count / ts,
             "speedup": ts / tb, "check_every": K, "block": st["block"], "grid": st["grid"],
             "converged": sum(x["status"] == P.MFC_OK for x in rb),
+            "at_cap": sum(x["status"] == P.MFC_NOT_CONVERGED for x in rb),
+            "nonfinite": sum(x["status"] == P.MFC_ERR_NONFINITE for x in rb),
+            "same_status": sum(x["status"] == r.status for x, (r, _, _) in zip(rb, rs)),
             "same_stop_step": sum(x["steps_flow"] == r.steps_flow for x, (r, _, _) in zip(rb, rs)),
             "max_rel_l2_u_batch_vs_alone": du, "max_rel_l2_c_batch_vs_alone": dc,
             "batched_mlups": upd / tb / 1e6, "mean_steps": upd / sum(w.nodes for w in works)}

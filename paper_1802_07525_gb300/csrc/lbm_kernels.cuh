@@ -293,9 +293,13 @@ __device__ __forceinline__ bool tile_on_open_boundary(const Geo &g, const int (&
 
 // Register caps of the step kernels: 2-D FP32 plain steps fit 32 registers (8 blocks of 256
 // threads per SM); 2-D FP16 plain steps (their conversions need more registers: 8% faster at 40
-// than at 32) and 2-D store/check steps 40; 3-D steps are left uncapped.
+// than at 32) and 2-D store/check steps 40.  3-D steps are latency-bound and gain from warps:
+// FP32 with 5 blocks of 256 threads (51 registers: 148 us per 256x128x128 step, against 211 us
+// uncapped at 128 registers) and FP16 with 4 (64 registers: 154 against 178 us); tighter caps
+// spill and run slower.
 template <int DIM, int MODE, typename ST = float> struct StepOccupancy {
-    static constexpr int blocks = DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4) ? 8 : 6) : 1;
+    static constexpr int blocks =
+        DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4) ? 8 : 6) : (sizeof(ST) == 4 ? 5 : 4);
 };
 
 // One step of node (x0 + threadIdx.x, y, z) of one lattice, in a tile of blockDim.x nodes from
@@ -497,9 +501,11 @@ template <int DIM, typename ST> struct BatchArgs {
 };
 
 // The tile loop and the shared argument block take registers of their own: 2-D batch steps are
-// capped at 48 registers (5 blocks of 256 threads per SM), where they do not spill.
+// capped at 48 registers (5 blocks of 256 threads per SM), where they do not spill; 3-D batch
+// steps take the caps of the 3-D step kernel.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
-__global__ void __launch_bounds__(256, DIM == 2 ? 5 : 1) lbm_batch_kernel(const BatchArgs<DIM, ST> b)
+__global__ void __launch_bounds__(256, DIM == 2 ? 5 : StepOccupancy<DIM, MODE, ST>::blocks)
+    lbm_batch_kernel(const BatchArgs<DIM, ST> b)
 {
     static_assert(sizeof(StepArgs<DIM, ST>) % 4 == 0, "argument block copied as 32-bit words");
     __shared__ StepArgs<DIM, ST> sa;  // arguments of the instance of the current tile
