@@ -157,3 +157,30 @@ def test_bad_requests_are_refused(P):
     with pytest.raises(P.MfcError):
         b.poll(t)  # the ticket was released
     b.close()
+
+
+@pytest.mark.parametrize("shape,bc", [
+    ((150, 37), (2, 1)),          # inlet/outlet along x, periodic y
+    ((96, 40), (1, 1)),           # fully periodic
+    ((20, 13, 30), (1, 0, 2)),    # periodic x, walls y, inlet/outlet along z
+])
+def test_batch_boundaries_match_oracle(P, shape, bc):
+    """The batch step takes inlet and transport-outlet values at the pulling node and writes only
+    periodic images and flow outlet values; after 200 fused steps its fields equal the FP64
+    oracle's within the per-step population tolerance."""
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N)
+    r = rng.random(N)
+    cls = np.where(r < 0.12, 3, np.where(r < 0.22, 4, 0)).astype(np.uint8)
+    kw = dict(tau=0.8, tau_c=0.7, u_in=0.02, c_in=1.0, k_sink=0.01)
+    b = P.Batch(check_every=50, block=128)
+    t = b.submit(shape, cls, bc=bc, tol_flow=0.0, tol_ade=0.0, max_steps=200, **kw)
+    b.run()
+    res = b.poll(t)
+    b.close()
+    o = oracle.Oracle(shape, cls, bc=bc, **kw)
+    o.step_coupled(200)
+    assert res["steps_flow"] == 200
+    assert np.max(np.abs(res["u"] - o.u)) < 1e-5
+    assert np.max(np.abs(res["c"] - o.conc)) < 1e-5
+    assert np.max(np.abs(res["rho"] - o.rho)) < 1e-5
