@@ -76,6 +76,10 @@ typedef struct {
     int nx, ny, nz;   /* lattice size; nz = 1 in 2-D */
     int bc[3];        /* boundary kind per axis */
     int precision;    /* MFC_FP32 or MFC_FP16_DEV (population storage) */
+    int ade_q;        /* transport velocity set: 0 for the default (D2Q5 in 2-D, D3Q7 in 3-D,
+                         with the linear equilibrium), or 9 in 2-D: D2Q9 with the equilibrium
+                         of Eq. 5, C in place of rho (the text after Eq. 12); batches take the
+                         default only */
     void *stream;     /* cudaStream_t, or NULL for a library-owned stream */
 } mfc_lattice_desc;
 

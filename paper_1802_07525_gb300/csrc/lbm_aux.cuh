@@ -80,11 +80,11 @@ __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, in
 
 // Link words from the node classes; (re)initialise populations and fields of nodes whose class
 // changed (or of every node when resetting); count the open nodes.
-template <int DIM> __global__ void build_links_kernel(const MaskArgs m)
+template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kernel(const MaskArgs m)
 {
     using F = FlowSet<DIM>;
-    using A = AdeSet<DIM>;
-    using LK = Links<DIM>;
+    using A = AdeSet<DIM, AQ>;
+    using LK = Links<DIM, AQ>;
     using LinkT = typename LK::T;
     const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;

@@ -50,10 +50,10 @@ struct Geo {
     }
 };
 
-template <int DIM, typename ST> struct StepArgs {
+template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     static constexpr int QF = FlowSet<DIM>::Q;
-    static constexpr int QA = AdeSet<DIM>::Q;
-    using LinkT = typename Links<DIM>::T;
+    static constexpr int QA = AdeSet<DIM, AQ>::Q;
+    using LinkT = typename Links<DIM, AQ>::T;
 
     Geo geo;
     int bc[3];            // boundary kind per axis
@@ -210,8 +210,8 @@ template <int DIM, typename ST> struct LazyGhosts {
 
 // Flow ghost writes of node p (stored at k) with velocity (u0, u1, u2) and link word L; the
 // node's post-collision populations are read back from pop, where this thread just stored them.
-template <int DIM, typename ST>
-__device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+template <int DIM, typename ST, int AQ>
+__device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                          long long k, uint32_t L, float u0, float u1, float u2)
 {
     using F = FlowSet<DIM>;
@@ -249,11 +249,11 @@ __device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST> &a, ST *pop,
 
 // Transport ghost writes of node p (stored at k) with link word L; the node's post-collision
 // populations are read back from pop.
-template <int DIM, typename ST>
-__device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+template <int DIM, typename ST, int AQ>
+__device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                         long long k, uint32_t L)
 {
-    using A = AdeSet<DIM>;
+    using A = AdeSet<DIM, AQ>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
     const int n[3] = {a.geo.nx, a.geo.ny, a.geo.nz};
@@ -265,7 +265,7 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST> &a, ST *pop, 
         ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei, LazyGhosts<DIM, ST>::value ? own : nullptr);
         if (!inout) continue;
         const int cf = A::c(i, FA);
-        if (p[FA] == 0 && cf == 1 && !((L >> (Links<DIM>::ADE_SELF + i)) & 1u)) {
+        if (p[FA] == 0 && cf == 1 && !((L >> (Links<DIM, AQ>::ADE_SELF + i)) & 1u)) {
             const int q0 = x - A::c(i, 0), q1 = y - A::c(i, 1), q2 = z - A::c(i, 2);
             st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2), a.gin_dev[i]);
         }
@@ -309,8 +309,8 @@ __device__ __forceinline__ bool step_writes_ghosts(const Geo &g, const int (&bc)
 // Flow ghost writes of a step: the periodic images of node p (its post-collision populations
 // read back from pop, where this thread just stored them) and, on the last layer of the
 // inlet/outlet axis, the outlet values from its velocity.
-template <int DIM, typename ST>
-__device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+template <int DIM, typename ST, int AQ>
+__device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                                  long long k, float u0, float u1, float u2)
 {
     using F = FlowSet<DIM>;
@@ -341,11 +341,11 @@ __device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST> &a, ST 
 }
 
 // Transport ghost writes of a step: the periodic images of node p.
-template <int DIM, typename ST>
-__device__ __forceinline__ void ade_ghosts_step(const StepArgs<DIM, ST> &a, ST *pop, int x, int y, int z,
+template <int DIM, typename ST, int AQ>
+__device__ __forceinline__ void ade_ghosts_step(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                                 long long k)
 {
-    using A = AdeSet<DIM>;
+    using A = AdeSet<DIM, AQ>;
     if (!on_periodic_boundary<DIM>(a.geo, a.bc, x, y, z)) return;
 #pragma unroll
     for (int i = 1; i < A::Q; ++i) {
@@ -387,8 +387,10 @@ template <int DIM, int MODE, typename ST = float> struct StepOccupancy {
 // Measured on GB300: the reader-side form makes the batch step 20% and the FP16 2-D step 6-7%
 // faster; the FP32 2-D step (32 registers) and the FP16 3-D step run faster in the writer form.
 enum : int { B_WRITER = 0, B_BOUNDARY = 1, B_INTERIOR = 2 };
-template <int DIM, typename ST> struct ReaderBoundaries {
-    static constexpr bool step = DIM == 2 && sizeof(ST) == 2;  // the single-lattice step kernel
+template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct ReaderBoundaries {
+    // the single-lattice step kernel; D2Q9 transport keeps writer-side ghosts, whose outlet
+    // values along the diagonals come from the neighbouring row
+    static constexpr bool step = DIM == 2 && sizeof(ST) == 2 && AQ == 5;
 };
 
 // One step of node (x0 + threadIdx.x, y, z) of one lattice, in a tile of blockDim.x nodes from
@@ -396,12 +398,14 @@ template <int DIM, typename ST> struct ReaderBoundaries {
 // a copy of the last node of the row, store nothing and add nothing, so that the whole block
 // joins the reduction.  acc receives the node's check-step terms.  BFORM: the boundary form
 // (B_BOUNDARY and B_INTERIOR are for tiles that do / do not touch an open boundary).
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM>
-__device__ __forceinline__ void step_node(const StepArgs<DIM, ST> &a, int x0, int y, int z, float (&acc)[NSUM])
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ>
+__device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, float (&acc)[NSUM])
 {
+    static_assert(BFORM == B_WRITER || AdeSet<DIM, AQ>::Q == default_aq<DIM>(),
+                  "reader-side boundaries take the transport outlet from the node itself: axis-aligned sets only");
     using F = FlowSet<DIM>;
-    using A = AdeSet<DIM>;
-    using LK = Links<DIM>;
+    using A = AdeSet<DIM, AQ>;
+    using LK = Links<DIM, AQ>;
     const Geo g = a.geo;
     const int x = x0 + threadIdx.x;
     if (MODE != MODE_CHECK && x >= g.nx) return;
@@ -555,13 +559,20 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST> &a, int x0, in
             cp += e[i];
         }
         const float sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : 0.0f;
+        float uu_ade = 0.f;
+        if (A::quadratic) {
+#pragma unroll
+            for (int ax = 0; ax < DIM; ++ax) uu_ade += u[ax] * u[ax];
+        }
         float moved = 0.f;
 #pragma unroll
         for (int i = 1; i < A::Q; ++i) {
             float cu = 0.f;
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cu += A::c(i, ax) * u[ax];
-            const float geq = A::w(i) * (cp + (a.c_ref + cp) * cu * A::inv_cs2);
+            // linear (D2Q5 / D3Q7) or the quadratic equilibrium of Eq. 5 (D2Q9), as deviations
+            const float shape = A::quadratic ? 3.0f * cu + 4.5f * cu * cu - 1.5f * uu_ade : cu * A::inv_cs2;
+            const float geq = A::w(i) * (cp + (a.c_ref + cp) * shape);
             const float v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - A::w(i) * sink);
             moved += v;
             if (valid) st(a.gdst + (long long)i * g.plane + k, v);
@@ -588,14 +599,14 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST> &a, int x0, in
 
 // One step of one lattice: one thread per node, grid (row / block, ny, nz); one reduction
 // partial per block on check steps.
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
-__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST>::blocks) lbm_step_kernel(const StepArgs<DIM, ST> a)
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>()>
+__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
     float acc[NSUM];
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
     const int x0 = blockIdx.x * blockDim.x;
-    if constexpr (ReaderBoundaries<DIM, ST>::step) {
+    if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
         if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, blockIdx.z))
             step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(a, x0, blockIdx.y, blockIdx.z, acc);
         else
@@ -687,12 +698,12 @@ __device__ __forceinline__ void batch_finalize_slot(const int2 range, const doub
 
 // Write the ghost cells of the current buffers (a.fdst, a.gdst) from the state they hold, after
 // the state was set from outside a step (geometry change, parameters, a population write).
-template <int DIM, typename ST>
-__global__ void fill_ghosts_kernel(const StepArgs<DIM, ST> a)
+template <int DIM, typename ST, int AQ = default_aq<DIM>()>
+__global__ void fill_ghosts_kernel(const StepArgs<DIM, ST, AQ> a)
 {
     using F = FlowSet<DIM>;
-    using A = AdeSet<DIM>;
-    using LK = Links<DIM>;
+    using A = AdeSet<DIM, AQ>;
+    using LK = Links<DIM, AQ>;
     const Geo &g = a.geo;
     const long long N = (long long)g.nx * g.ny * g.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;

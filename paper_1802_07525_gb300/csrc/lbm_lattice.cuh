@@ -3,7 +3,9 @@
 //
 // D2Q9 follows Eqs. 1-3 and the weights of Eqs. 6-8; the order of c5..c8 is the one fixed by the
 // bounce-back pairs of Eq. 11 (5<->7, 2<->4, 6<->8).  D3Q19 (3-D flow) has the rest velocity, six
-// faces and twelve edges with opposites adjacent; D2Q5 / D3Q7 carry the substrate (Eq. 12).
+// faces and twelve edges with opposites adjacent; D2Q5 / D3Q7 carry the substrate (Eq. 12) with
+// the linear equilibrium, and, as the text after Eq. 12 has it, D2Q9 with the equilibrium of
+// Eq. 5 (C in place of rho) is the paper-literal alternative in 2-D.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -20,7 +22,9 @@ enum : uint8_t { CLS_FLOW = 1, CLS_ADE = 2, CLS_SINK = 4 };
 // ---- velocity sets ---------------------------------------------------------------------------
 
 template <int DIM> struct FlowSet;
-template <int DIM> struct AdeSet;
+// Transport velocity set: AQ = 5 (D2Q5) or 9 (D2Q9, quadratic equilibrium) in 2-D, 7 in 3-D.
+template <int DIM> __host__ __device__ constexpr int default_aq() { return DIM == 2 ? 5 : 7; }
+template <int DIM, int AQ = default_aq<DIM>()> struct AdeSet;
 
 template <> struct FlowSet<2> {
     static constexpr int Q = 9;
@@ -61,30 +65,43 @@ template <> struct FlowSet<3> {
     }
 };
 
-template <> struct AdeSet<2> {
+template <> struct AdeSet<2, 5> {
     static constexpr int Q = 5;
+    static constexpr bool quadratic = false;  // G_i^eq = w_i C (1 + c_i.u / cs^2)
     static constexpr float inv_cs2 = 3.0f;  // D = (tau_c - 1/2) / 3
     __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<2>::c(i, a); }
     __host__ __device__ static constexpr int opp(int i) { return FlowSet<2>::opp(i); }
     __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 3.0f : 1.0f / 6.0f; }
 };
 
-template <> struct AdeSet<3> {
+template <> struct AdeSet<3, 7> {
     static constexpr int Q = 7;
+    static constexpr bool quadratic = false;
     static constexpr float inv_cs2 = 4.0f;  // D = (tau_c - 1/2) / 4
     __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<3>::c(i, a); }
     __host__ __device__ static constexpr int opp(int i) { return FlowSet<3>::opp(i); }
     __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 4.0f : 1.0f / 8.0f; }
 };
 
+// D2Q9 transport with the flow equilibrium of Eq. 5 (C in place of rho):
+// G_i^eq = w_i C (1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 u.u); D = (tau_c - 1/2) / 3.
+template <> struct AdeSet<2, 9> {
+    static constexpr int Q = 9;
+    static constexpr bool quadratic = true;
+    static constexpr float inv_cs2 = 3.0f;
+    __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<2>::c(i, a); }
+    __host__ __device__ static constexpr int opp(int i) { return FlowSet<2>::opp(i); }
+    __host__ __device__ static constexpr float w(int i) { return FlowSet<2>::w(i); }
+};
+
 // ---- link masks ------------------------------------------------------------------------------
 // One word per node.  Bit 0: the node is blocked for the flow.  Bit i (1..Qf-1): the flow
 // population arriving along c_i bounces back (its source is a wall or a blocked node).
 // Bit Qf: blocked for transport.  Bit Qf+i (1..Qa-1): the transport population along c_i
-// bounces back.  Bit Qf+Qa: consumption node.
-template <int DIM> struct Links {
+// bounces back.  Bit Qf+Qa: consumption node.  16-bit words when they fit (D2Q9 + D2Q5), else 32.
+template <int DIM, int AQ = default_aq<DIM>()> struct Links {
     static constexpr int QF = FlowSet<DIM>::Q;
-    static constexpr int QA = AdeSet<DIM>::Q;
+    static constexpr int QA = AdeSet<DIM, AQ>::Q;
     static constexpr int FLOW_SELF = 0;
     static constexpr int ADE_SELF = QF;
     static constexpr int SINK = QF + QA;

@@ -1,6 +1,7 @@
-// Launchers of the step, batch-step and ghost-fill kernels for one dimension (MFC_DIM) and one
-// storage type (MFC_ST), included by one translation unit per pair so that the instantiations
-// compile in parallel.
+// Launchers of the step, batch-step and ghost-fill kernels for one dimension (MFC_DIM), one
+// storage type (MFC_ST) and one transport velocity set (MFC_AQ, default D2Q5 / D3Q7), included
+// by one translation unit per combination so that the instantiations compile in parallel.  The
+// batch launchers exist for the default transport sets only (MFC_BATCH_FN defined).
 #include <string.h>
 
 #include "mfc_internal.h"
@@ -15,35 +16,41 @@ namespace {
 
 using ST = MFC_ST;
 constexpr int D = MFC_DIM;
+#ifdef MFC_AQ
+constexpr int AQ = MFC_AQ;
+#else
+constexpr int AQ = default_aq<D>();
+#endif
+using Args = StepArgs<D, ST, AQ>;
 
 template <bool FLOW, bool ADE>
-cudaError_t launch_mode(const StepArgs<D, ST> &a, const StepHost &h, cudaStream_t s)
+cudaError_t launch_mode(const Args &a, const StepHost &h, cudaStream_t s)
 {
     const dim3 grid((unsigned)h.grid, (unsigned)h.geo.ny, (unsigned)h.geo.nz);
     switch (h.mode) {
-    case MODE_PLAIN: lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN><<<grid, h.block, 0, s>>>(a); break;
-    case MODE_WRITE: lbm_step_kernel<D, ST, FLOW, ADE, MODE_WRITE><<<grid, h.block, 0, s>>>(a); break;
-    default: lbm_step_kernel<D, ST, FLOW, ADE, MODE_CHECK><<<grid, h.block, 0, s>>>(a); break;
+    case MODE_PLAIN: lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ><<<grid, h.block, 0, s>>>(a); break;
+    case MODE_WRITE: lbm_step_kernel<D, ST, FLOW, ADE, MODE_WRITE, AQ><<<grid, h.block, 0, s>>>(a); break;
+    default: lbm_step_kernel<D, ST, FLOW, ADE, MODE_CHECK, AQ><<<grid, h.block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
-StepArgs<D, ST> make_args(const StepHost &h)
+Args make_args(const StepHost &h)
 {
-    StepArgs<D, ST> a;
+    Args a;
     a.geo = h.geo;
     for (int i = 0; i < 3; ++i) a.bc[i] = h.bc[i];
     a.fsrc = static_cast<const ST *>(h.fsrc);
     a.fdst = static_cast<ST *>(h.fdst);
     a.gsrc = static_cast<const ST *>(h.gsrc);
     a.gdst = static_cast<ST *>(h.gdst);
-    a.link = static_cast<const typename Links<D>::T *>(h.link);
+    a.link = static_cast<const typename Links<D, AQ>::T *>(h.link);
     a.fld_rho = h.fld_rho; a.fld_u = h.fld_u; a.fld_c = h.fld_c;
     a.partials = h.partials;
     a.omega = h.omega; a.omega_c = h.omega_c; a.k_sink = h.k_sink; a.u_scale = h.u_scale;
     a.rho_out = h.rho_out; a.c_ref = h.c_ref; a.ade_dirichlet = h.ade_dirichlet;
-    for (int i = 0; i < StepArgs<D, ST>::QF; ++i) a.bb_in[i] = h.bb_in[i];
-    for (int i = 0; i < StepArgs<D, ST>::QA; ++i) {
+    for (int i = 0; i < Args::QF; ++i) a.bb_in[i] = h.bb_in[i];
+    for (int i = 0; i < Args::QA; ++i) {
         a.gin_dev[i] = h.gin_dev[i];
         a.gout_dev[i] = h.gout_dev[i];
     }
@@ -54,7 +61,7 @@ StepArgs<D, ST> make_args(const StepHost &h)
 
 cudaError_t MFC_STEP_FN(StepHost &h, cudaStream_t s)
 {
-    const StepArgs<D, ST> a = make_args(h);
+    const Args a = make_args(h);
     h.nblocks = h.grid * h.geo.ny * h.geo.nz;
     switch (h.kind) {
     case KIND_COUPLED: return launch_mode<true, true>(a, h, s);
@@ -63,9 +70,10 @@ cudaError_t MFC_STEP_FN(StepHost &h, cudaStream_t s)
     }
 }
 
+#ifdef MFC_BATCH_FN
 size_t MFC_ARGS_FN(const StepHost &h, void *out)
 {
-    const StepArgs<D, ST> a = make_args(h);
+    const Args a = make_args(h);
     if (out) memcpy(out, &a, sizeof a);
     return sizeof a;
 }
@@ -98,13 +106,14 @@ int MFC_OCC_FN(int block)
     }
     return n > 0 ? n : 1;
 }
+#endif
 
 cudaError_t MFC_FILL_FN(const StepHost &h, cudaStream_t s)
 {
-    const StepArgs<D, ST> a = make_args(h);
+    const Args a = make_args(h);
     const long long N = (long long)h.geo.nx * h.geo.ny * h.geo.nz;
     const long long b = (N + 255) / 256;
-    fill_ghosts_kernel<D, ST><<<(int)(b < 65535 ? b : 65535), 256, 0, s>>>(a);
+    fill_ghosts_kernel<D, ST, AQ><<<(int)(b < 65535 ? b : 65535), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

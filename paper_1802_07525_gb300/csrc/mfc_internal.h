@@ -16,6 +16,7 @@ enum : int { DEFAULT_BLOCK = 128 };
 // Everything a step launch needs, independent of dimension and storage type.
 struct StepHost {
     int dim, half;
+    int aq;  // transport velocity set: 5 / 7 (default) or 9 (D2Q9, 2-D)
     int kind, mode;
     Geo geo;
     int bc[3];
@@ -30,7 +31,7 @@ struct StepHost {
     double *partials;
     float omega, omega_c, k_sink, u_scale, rho_out, c_ref;
     int ade_dirichlet;
-    float bb_in[19], gin_dev[7], gout_dev[7];
+    float bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
 };
 
 // One launch of the batch step kernel over a tile table (coupled steps).
@@ -53,6 +54,10 @@ cudaError_t launch_fill_ghosts_2d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_2d_f16(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_3d_f16(const StepHost &h, cudaStream_t s);
+cudaError_t launch_step_2d9_f32(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_2d9_f16(StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d9_f32(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d9_f16(const StepHost &h, cudaStream_t s);
 
 cudaError_t launch_batch_2d_f32(const BatchHost &h, cudaStream_t s);
 cudaError_t launch_batch_2d_f16(const BatchHost &h, cudaStream_t s);
@@ -90,16 +95,18 @@ inline size_t step_args(const StepHost &h, void *out)
 
 inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
 {
+    if (h.dim == 2 && h.aq == 9) return h.half ? launch_step_2d9_f16(h, s) : launch_step_2d9_f32(h, s);
     if (h.dim == 2) return h.half ? launch_step_2d_f16(h, s) : launch_step_2d_f32(h, s);
     return h.half ? launch_step_3d_f16(h, s) : launch_step_3d_f32(h, s);
 }
 
 inline cudaError_t launch_fill_ghosts(const StepHost &h, cudaStream_t s)
 {
+    if (h.dim == 2 && h.aq == 9) return h.half ? launch_fill_ghosts_2d9_f16(h, s) : launch_fill_ghosts_2d9_f32(h, s);
     if (h.dim == 2) return h.half ? launch_fill_ghosts_2d_f16(h, s) : launch_fill_ghosts_2d_f32(h, s);
     return h.half ? launch_fill_ghosts_3d_f16(h, s) : launch_fill_ghosts_3d_f32(h, s);
 }
-cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s);
+cudaError_t launch_links(int dim, int aq, const MaskArgs &m, cudaStream_t s);
 cudaError_t launch_grow(int dim, const GrowArgs &g, cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *stage1, double *results,
                             cudaStream_t s);

@@ -23,11 +23,12 @@
 
 namespace mfc {
 
-cudaError_t launch_links(int dim, const MaskArgs &m, cudaStream_t s)
+cudaError_t launch_links(int dim, int aq, const MaskArgs &m, cudaStream_t s)
 {
     const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
     const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
-    if (dim == 2) build_links_kernel<2><<<blocks, 256, 0, s>>>(m);
+    if (dim == 2 && aq == 9) build_links_kernel<2, 9><<<blocks, 256, 0, s>>>(m);
+    else if (dim == 2) build_links_kernel<2><<<blocks, 256, 0, s>>>(m);
     else build_links_kernel<3><<<blocks, 256, 0, s>>>(m);
     return cudaGetLastError();
 }
@@ -162,6 +163,10 @@ mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
         *why = "precision must be MFC_FP32 or MFC_FP16_DEV";
         return MFC_ERR_ARG;
     }
+    if (!(d->ade_q == 0 || (d->dim == 2 && (d->ade_q == 5 || d->ade_q == 9)) || (d->dim == 3 && d->ade_q == 7))) {
+        *why = "ade_q must be 0 (default), 5 or 9 in 2-D, 7 in 3-D";
+        return MFC_ERR_ARG;
+    }
     return MFC_OK;
 }
 
@@ -180,7 +185,7 @@ Layout layout_of(const mfc_lattice_desc *d)
     Layout l;
     l.dim = d->dim;
     l.qf = d->dim == 2 ? 9 : 19;
-    l.qa = d->dim == 2 ? 5 : 7;
+    l.qa = d->dim == 2 ? (d->ade_q == 9 ? 9 : 5) : 7;
     Geo &g = l.geo;
     g.nx = d->nx;
     g.ny = d->ny;
@@ -194,7 +199,7 @@ Layout layout_of(const mfc_lattice_desc *d)
     g.plane = (long long)round_up((size_t)(last + 2 * g.px + 64), 64);
     l.N = (long long)g.nx * g.ny * g.nz;
     l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
-    l.link_bytes = d->dim == 2 ? 2 : 4;
+    l.link_bytes = (d->dim == 2 && l.qa == 5) ? 2 : 4;  // 9 + 9 + 1 link bits need 32-bit words
     return l;
 }
 
@@ -246,13 +251,26 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
         const double w = L->dim == 2 ? FlowSet<2>::w(i) : FlowSet<3>::w(i);
         h->bb_in[i] = (float)(2.0 * w * p.rho_in * ci * p.u_in * 3.0);
     }
+    // transport inlet (and Dirichlet outlet) equilibria at the inlet velocity: linear on D2Q5 /
+    // D3Q7, the quadratic form of Eq. 5 on D2Q9
     const double inv_cs2 = L->dim == 2 ? 3.0 : 4.0;
     for (int i = 0; i < L->qa; ++i) {
-        const int ci = L->dim == 2 ? AdeSet<2>::c(i, fa) : AdeSet<3>::c(i, fa);
-        const double w = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
-        h->gin_dev[i] = (float)(w * p.c_in * (1.0 + ci * p.u_in * inv_cs2) - w * L->c_ref);
-        h->gout_dev[i] = (float)(w * p.c_out * (1.0 + ci * p.u_in * inv_cs2) - w * L->c_ref);
+        int ci;
+        double w, shape;
+        if (L->qa == 9) {
+            ci = AdeSet<2, 9>::c(i, fa);
+            w = AdeSet<2, 9>::w(i);
+            const double cu = ci * p.u_in;
+            shape = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * p.u_in * p.u_in;
+        } else {
+            ci = L->dim == 2 ? AdeSet<2>::c(i, fa) : AdeSet<3>::c(i, fa);
+            w = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
+            shape = 1.0 + ci * p.u_in * inv_cs2;
+        }
+        h->gin_dev[i] = (float)(w * p.c_in * shape - w * L->c_ref);
+        h->gout_dev[i] = (float)(w * p.c_out * shape - w * L->c_ref);
     }
+    h->aq = L->qa;
 }
 
 namespace {
@@ -505,7 +523,7 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
     m.c_ref = L->c_ref;
     m.counts = L->counts_d;
     CK(L, cudaMemsetAsync(L->counts_d, 0, 2 * sizeof(unsigned long long), L->stream));
-    CK(L, launch_links(L->dim, m, L->stream));
+    CK(L, launch_links(L->dim, L->qa, m, L->stream));
     mfc_status st = fill_ghosts(L);
     if (st != MFC_OK) return st;
     CK(L, cudaMemcpyAsync(L->counts_h, L->counts_d, 2 * sizeof(unsigned long long),
@@ -557,7 +575,7 @@ mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *p
     L->N = l.N;
     L->st_bytes = l.st;
     L->half = desc->precision == MFC_FP16_DEV;
-    L->link32 = desc->dim == 3;
+    L->link32 = l.link_bytes == 4;
     // transport storage offset: 0, so that the no-substrate start state is stored exactly
     L->c_ref = 0.0f;
     cudaGetDevice(&L->device);
@@ -843,7 +861,8 @@ static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const doub
         a.half = L->half;
         a.self_bit = L->qf;
         a.offset = L->c_ref;
-        for (int i = 0; i < a.q; ++i) a.w[i] = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
+        for (int i = 0; i < a.q; ++i)
+            a.w[i] = L->qa == 9 ? AdeSet<2, 9>::w(i) : (L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i));
     } else if (which == MFC_FIELD_VELOCITY) {
         a.q = L->dim;
         a.pop = L->fld_u;

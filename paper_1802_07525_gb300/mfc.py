@@ -31,7 +31,7 @@ MFC_POP_FLOW, MFC_POP_ADE, MFC_FIELD_VELOCITY = 0, 1, 2
 class LatticeDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("ade_q", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -182,7 +182,7 @@ def make_params(tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0
     return Params(tau, tau_c, u_in, rho_in, rho_out, c_in, c_out, k_sink, u_scale, ade_outlet)
 
 
-def make_desc(shape, bc=None, precision=MFC_FP32, stream=None) -> LatticeDesc:
+def make_desc(shape, bc=None, precision=MFC_FP32, stream=None, ade_q=0) -> LatticeDesc:
     shape = tuple(int(s) for s in shape)
     dim = len(shape)
     if bc is None:
@@ -195,25 +195,28 @@ def make_desc(shape, bc=None, precision=MFC_FP32, stream=None) -> LatticeDesc:
     for a in range(3):
         d.bc[a] = bcs[a]
     d.precision = precision
+    d.ade_q = ade_q
     d.stream = stream
     return d
 
 
-def lattice_bytes(shape, bc=None, precision=MFC_FP32) -> int:
-    return int(lib().mfc_lattice_bytes(ctypes.byref(make_desc(shape, bc, precision))))
+def lattice_bytes(shape, bc=None, precision=MFC_FP32, ade_q=0) -> int:
+    return int(lib().mfc_lattice_bytes(ctypes.byref(make_desc(shape, bc, precision, None, ade_q))))
 
 
 class Lattice:
     """One lattice resident on the current CUDA device (see ``include/mfc.h``)."""
 
-    def __init__(self, shape, *, bc=None, precision=MFC_FP32, stream=None, **params):
+    def __init__(self, shape, *, bc=None, precision=MFC_FP32, stream=None, ade_q=0, **params):
+        """ade_q: 0 for the default transport set (D2Q5 / D3Q7), 9 for D2Q9 with the equilibrium
+        of Eq. 5 (2-D)."""
         self.shape = tuple(int(s) for s in shape)
         self.dim = len(self.shape)
         self.N = int(np.prod(self.shape))
         self.qf = 9 if self.dim == 2 else 19
-        self.qa = 5 if self.dim == 2 else 7
+        self.qa = (9 if ade_q == 9 else 5) if self.dim == 2 else 7
         self._L = lib()
-        self.desc = make_desc(self.shape, bc, precision, stream)
+        self.desc = make_desc(self.shape, bc, precision, stream, ade_q)
         self.params = make_params(**params)
         h = ctypes.c_void_p()
         st = self._L.mfc_create_lattice(ctypes.byref(self.desc), ctypes.byref(self.params),

@@ -379,3 +379,73 @@ def test_launch_variants_agree(P, shape, bc, prec):
         assert maxabs(out[1], ref[1]) < tol, v
         assert maxabs(out[2], ref[2]) < tol, v
         assert np.allclose(out[3], ref[3], rtol=1e-3 if prec else 1e-5, atol=1e-12), v
+
+
+# ------------------------------------------------------------------------------------------
+# Paper-literal transport: D2Q9 with the equilibrium of Eq. 5 (C in place of rho)
+# ------------------------------------------------------------------------------------------
+
+def test_d2q9_transport_channel_populations_first_1000_steps(P):
+    """Fused flow + D2Q9 transport on the 128x64 channel: populations within 1e-5 of the
+    oracle's D2Q9 transport at steps 1, 10, 100, 1000."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, ade_q=9, **channel_kw(w))
+    assert g.qa == 9 and o.qa == 9
+    done = 0
+    for target in (1, 10, 100, 1000):
+        g.step_coupled(target - done)
+        o.step_coupled(target - done)
+        done = target
+        assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL, target
+        assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL, target
+    _, u, c, _ = g.read_fields()
+    assert maxabs(c, o.conc) < POP_TOL
+
+
+@pytest.mark.parametrize("shape,bc,outlet", [
+    ((150, 37), (2, 1), 0),   # inlet/outlet along x, periodic y, ragged rows
+    ((133, 20), (2, 0), 1),   # walls, Dirichlet transport outlet
+    ((64, 24), (1, 1), 0),    # fully periodic
+])
+def test_d2q9_transport_boundary_kinds(P, shape, bc, outlet):
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N + 9)
+    r = rng.random(N)
+    cls = np.where(r < 0.12, 3, np.where(r < 0.22, 4, np.where(r < 0.26, 5, 0))).astype(np.uint8)
+    kw = dict(tau=0.75, tau_c=0.8, u_in=0.03, c_in=1.0, c_out=0.25, k_sink=0.01, ade_outlet=outlet)
+    g, o = pair(P, shape, cls, bc=bc, ade_q=9, **kw)
+    g.step_coupled(300)
+    o.step_coupled(300)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+
+
+def test_d2q9_transport_steady_fields_and_current(P):
+    """Both sides to tol 1e-7 (cap 10^4, a check every 100 steps): steady fields within 1e-4
+    relative L2 and the current within 1e-4."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, ade_q=9, **channel_kw(w))
+    rg = g.solve_steady(mode=1, tol_flow=1e-7, tol_ade=1e-7, max_steps=10000, check_every=100)
+    ro = o.solve_steady(mode=1, tol_flow=1e-7, tol_ade=1e-7, max_steps=10000, check_every=100)
+    _, u, c, _ = g.read_fields()
+    assert rel_l2(u, o.u) < FIELD_TOL
+    assert rel_l2(c, o.conc) < FIELD_TOL
+    assert abs(rg.current - ro.current) / ro.current < FIELD_TOL
+
+
+def test_d2q9_transport_launch_shapes_agree_and_fp16_bound(P):
+    w = mi.channel_128x64()
+    out = []
+    for block in (128, 256):
+        g = P.Lattice(w.shape, ade_q=9, **channel_kw(w))
+        g.set_geometry(w.cls)
+        g.set_launch(block=block)
+        g.step_coupled(500)
+        out.append(g.read_populations(P.MFC_POP_ADE))
+        g.close()
+    assert maxabs(out[0], out[1]) < 2e-6
+    g, o = pair(P, w.shape, w.cls, precision=1, ade_q=9, **channel_kw(w))
+    g.step_coupled(1000)
+    o.step_coupled(1000)
+    _, u, c, _ = g.read_fields()
+    assert rel_l2(u, o.u) < 2e-2 and rel_l2(c, o.conc) < 1e-2
