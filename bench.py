@@ -10,8 +10,9 @@ every block is taken).  The working set (2 x 14 planes x 4 B x 2.1 M nodes = 235
 populations) is larger than the 129 MB L2, so no explicit flush is needed between steps.
 
 Further legs on one GPU (rank 0 of a 1-GPU run), each reported in the same JSON line:
-  variants  - the FP16-storage 2-D step and the 3-D 256x128x128 electrode (FP32, FP16):
-              MLUPS and fraction of the HBM roofline;
+  variants  - the FP16-storage 2-D step, the 2-D step with the paper-literal D2Q9 transport,
+              and the 3-D 256x128x128 electrode (FP32, FP16): MLUPS and fraction of the HBM
+              roofline;
   accuracy  - FP32 and FP16 results against the FP64 oracle (populations after a fixed number
               of steps, steady fields and current), the oracle running in spawned processes
               while the GPU legs run;
@@ -311,10 +312,12 @@ def time_plain_steps(P, lat, stream, M=400):
     return e0.elapsed_time(e1) / M
 
 
-def step_bytes(dim, prec_bytes, flow_open, ade_open):
+def step_bytes(dim, prec_bytes, flow_open, ade_open, ade_q=0):
     """Algorithmic bytes of one fused step: every population of every open node read once and
     written once."""
     qf, qa = (9, 5) if dim == 2 else (19, 7)
+    if ade_q:
+        qa = ade_q
     return 2 * prec_bytes * (qf * flow_open + qa * ade_open)
 
 
@@ -326,11 +329,13 @@ def leg_variants(P, peak):
     out = {}
     # the FP16 2-D case runs on 4096x1024: its 2048x1024 working set (118 MB) would fit the L2
     cases = [("2d_4096x1024_fp16", mi.anode_2d(4096, 1024), P.MFC_FP16_DEV, 10000),
+             ("2d_2048x1024_d2q9_transport_fp32", mi.anode_2d(), P.MFC_FP32, 10000),
              ("3d_256x128x128_fp32", mi.electrode_3d(), P.MFC_FP32, 5000),
              ("3d_256x128x128_fp16", mi.electrode_3d(), P.MFC_FP16_DEV, 5000)]
     for name, w, prec, steps in cases:
         stream = torch.cuda.Stream()
-        lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, **wkw(w))
+        aq = 9 if "d2q9" in name else 0
+        lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, ade_q=aq, **wkw(w))
         lat.set_geometry(w.cls)
         fo, ao = lat.active_nodes()
         lat.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=1000,
@@ -345,7 +350,7 @@ def leg_variants(P, peak):
         ms = e0.elapsed_time(e1)
         kern_ms = time_plain_steps(P, lat, stream)
         sb = 2 if prec == P.MFC_FP16_DEV else 4
-        byt = step_bytes(w.dim, sb, fo, ao)
+        byt = step_bytes(w.dim, sb, fo, ao, aq)
         ach = byt / (kern_ms * 1e-3) / 1e9
         out[name] = {"mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
                      "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": byt,

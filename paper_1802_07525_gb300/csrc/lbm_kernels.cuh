@@ -369,13 +369,13 @@ __device__ __forceinline__ bool tile_on_open_boundary(const Geo &g, const int (&
 
 // Register caps of the step kernels: 2-D FP32 plain steps fit 32 registers (8 blocks of 256
 // threads per SM); 2-D FP16 plain steps (their conversions need more registers: 8% faster at 40
-// than at 32) and 2-D store/check steps 40.  3-D steps are latency-bound and gain from warps:
+// than at 32), FP32 2-D steps with D2Q9 transport, and 2-D store/check steps 40.  3-D steps are latency-bound and gain from warps:
 // FP32 with 5 blocks of 256 threads (51 registers: 148 us per 256x128x128 step, against 211 us
 // uncapped at 128 registers) and FP16 with 4 (64 registers: 154 against 178 us); tighter caps
 // spill and run slower.
-template <int DIM, int MODE, typename ST = float> struct StepOccupancy {
+template <int DIM, int MODE, typename ST = float, int AQ = default_aq<DIM>()> struct StepOccupancy {
     static constexpr int blocks =
-        DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4) ? 8 : 6) : (sizeof(ST) == 4 ? 5 : 4);
+        DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4 && AQ == 5) ? 8 : 6) : (sizeof(ST) == 4 ? 5 : 4);
 };
 
 // Two equivalent ways to realise the open boundaries in a step, chosen per kernel by measurement:
@@ -600,7 +600,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 // One step of one lattice: one thread per node, grid (row / block, ny, nz); one reduction
 // partial per block on check steps.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>()>
-__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
+__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
     float acc[NSUM];
 #pragma unroll
