@@ -31,8 +31,10 @@
  *   - Errors: every call returns an mfc_status; nothing aborts or exits.  A CUDA error is
  *     recorded on the lattice and returned by that call and every later call on it.
  *   - Precision: flow populations are stored as deviations from rest (f_i - w_i), transport
- *     populations as they are (g_i), in FP32 (MFC_FP32) or FP16 (MFC_FP16_DEV); arithmetic is
- *     FP32; residual, mass and current sums are FP64.
+ *     populations as they are (g_i), in FP32 (MFC_FP32) or FP16 (MFC_FP16_DEV) with FP32
+ *     arithmetic and FP32 fields, or in FP64 with FP64 arithmetic and FP64 fields (MFC_FP64:
+ *     the same kernels instantiated in double, a parity reference for the FP64 method of the
+ *     paper, single lattices only); residual, mass and current sums are FP64.
  */
 #ifndef MFC_H
 #define MFC_H
@@ -66,7 +68,7 @@ typedef enum {
 } mfc_status;
 
 enum { MFC_BC_WALL = 0, MFC_BC_PERIODIC = 1, MFC_BC_INOUT = 2 };
-enum { MFC_FP32 = 0, MFC_FP16_DEV = 1 };
+enum { MFC_FP32 = 0, MFC_FP16_DEV = 1, MFC_FP64 = 2 };
 enum { MFC_SEQUENTIAL = 0, MFC_CONCURRENT = 1 };
 enum { MFC_OUTLET_ZERO_GRADIENT = 0, MFC_OUTLET_DIRICHLET = 1 };
 enum { MFC_POP_FLOW = 0, MFC_POP_ADE = 1, MFC_FIELD_VELOCITY = 2 };
@@ -75,7 +77,8 @@ typedef struct {
     int dim;          /* 2 or 3 */
     int nx, ny, nz;   /* lattice size; nz = 1 in 2-D */
     int bc[3];        /* boundary kind per axis */
-    int precision;    /* MFC_FP32 or MFC_FP16_DEV (population storage) */
+    int precision;    /* MFC_FP32, MFC_FP16_DEV or MFC_FP64 (population storage; MFC_FP64
+                         also computes in FP64); batches take MFC_FP32 or MFC_FP16_DEV */
     int ade_q;        /* transport velocity set: 0 for the default (D2Q5 in 2-D, D3Q7 in 3-D,
                          with the linear equilibrium), or 9 in 2-D: D2Q9 with the equilibrium
                          of Eq. 5, C in place of rho (the text after Eq. 12); batches take the

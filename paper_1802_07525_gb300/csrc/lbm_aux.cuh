@@ -45,6 +45,17 @@ __global__ void __launch_bounds__(256) finalize_stage2_kernel(const double *stag
     }
 }
 
+// Fields are stored in the lattice's arithmetic type: FP64 in the FP64 instantiation, else FP32.
+__device__ __forceinline__ double load_field(const void *p, int dbl, long long k)
+{
+    return dbl ? reinterpret_cast<const double *>(p)[k] : (double)reinterpret_cast<const float *>(p)[k];
+}
+__device__ __forceinline__ void store_field(void *p, int dbl, long long k, double v)
+{
+    if (dbl) reinterpret_cast<double *>(p)[k] = v;
+    else reinterpret_cast<float *>(p)[k] = (float)v;
+}
+
 __device__ __forceinline__ void node_xyz(const Geo &g, long long q, int *x, int *y, int *z)
 {
     *x = (int)(q % g.nx);
@@ -109,6 +120,7 @@ template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kerne
         if (f_open && (o & CLS_FLOW)) {  // opens up (or reset): flow at rest
             for (int i = 0; i < F::Q; ++i) {
                 if (m.half) reinterpret_cast<__half *>(m.fpop)[i * m.geo.plane + k] = __float2half_rn(0.f);
+                else if (m.dbl) reinterpret_cast<double *>(m.fpop)[i * m.geo.plane + k] = 0.0;
                 else reinterpret_cast<float *>(m.fpop)[i * m.geo.plane + k] = 0.f;
             }
         }
@@ -116,14 +128,15 @@ template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kerne
             for (int i = 0; i < A::Q; ++i) {
                 const float v = -A::w(i) * m.c_ref;
                 if (m.half) reinterpret_cast<__half *>(m.gpop)[i * m.geo.plane + k] = __float2half_rn(v);
+                else if (m.dbl) reinterpret_cast<double *>(m.gpop)[i * m.geo.plane + k] = -A::wd(i) * (double)m.c_ref;
                 else reinterpret_cast<float *>(m.gpop)[i * m.geo.plane + k] = v;
             }
         }
         if (m.reset || !f_open) {
-            m.fld_rho[k] = 0.f;
-            for (int ax = 0; ax < DIM; ++ax) m.fld_u[ax * m.geo.plane + k] = 0.f;
+            store_field(m.fld_rho, m.dbl, k, 0.0);
+            for (int ax = 0; ax < DIM; ++ax) store_field(m.fld_u, m.dbl, ax * m.geo.plane + k, 0.0);
         }
-        if (m.reset || !a_open) m.fld_c[k] = -m.c_ref;
+        if (m.reset || !a_open) store_field(m.fld_c, m.dbl, k, -(double)m.c_ref);
         if (f_open) atomicAdd(&m.counts[0], 1ull);
         if (a_open) atomicAdd(&m.counts[1], 1ull);
     }
@@ -146,11 +159,16 @@ __global__ void fields_to_dense_kernel(const ConvArgs a)
         const long long k = a.geo.at(x, y, z);
         const uint32_t L = read_link(a.link, a.link32, k);
         const bool fo = !(L & (1u << a.flow_self)), ao = !(L & (1u << a.ade_self));
-        if (a.rho) a.rho[q] = fo ? 1.0 + (double)a.fld_rho[k] : 0.0;
+        if (a.rho) a.rho[q] = fo ? 1.0 + load_field(a.fld_rho, a.dbl, k) : 0.0;
         if (a.u)
             for (int ax = 0; ax < a.dim; ++ax)
-                a.u[ax * N + q] = fo ? (double)a.fld_u[ax * a.geo.plane + k] : 0.0;
-        if (a.c) a.c[q] = ao ? (double)(a.c_ref + a.fld_c[k]) : 0.0;
+                a.u[ax * N + q] = fo ? load_field(a.fld_u, a.dbl, ax * a.geo.plane + k) : 0.0;
+        if (a.c) {
+            // C = c_ref + (C - c_ref), added in the storage's arithmetic
+            const double cd = a.dbl ? (double)a.c_ref + load_field(a.fld_c, 1, k)
+                                    : (double)(a.c_ref + reinterpret_cast<const float *>(a.fld_c)[k]);
+            a.c[q] = ao ? cd : 0.0;
+        }
     }
 }
 
@@ -168,15 +186,17 @@ __global__ void pop_convert_kernel(const PopArgs a)
             if (a.to_dense) {
                 double v = 0.0;
                 if (open) {
-                    const float dv = a.half ? __half2float(reinterpret_cast<const __half *>(a.pop)[p])
-                                            : reinterpret_cast<const float *>(a.pop)[p];
-                    v = (double)dv + (double)a.w[i] * (double)a.offset;
+                    const double dv = a.half  ? (double)__half2float(reinterpret_cast<const __half *>(a.pop)[p])
+                                      : a.dbl ? reinterpret_cast<const double *>(a.pop)[p]
+                                              : (double)reinterpret_cast<const float *>(a.pop)[p];
+                    v = dv + a.w[i] * a.offset;
                 }
                 a.dense[i * N + q] = v;
             } else {
-                const float dv = (float)(a.dense[i * N + q] - (double)a.w[i] * (double)a.offset);
-                if (a.half) reinterpret_cast<__half *>(a.pop)[p] = __float2half_rn(dv);
-                else reinterpret_cast<float *>(a.pop)[p] = dv;
+                const double dv = a.dense[i * N + q] - a.w[i] * a.offset;
+                if (a.half) reinterpret_cast<__half *>(a.pop)[p] = __float2half_rn((float)dv);
+                else if (a.dbl) reinterpret_cast<double *>(a.pop)[p] = dv;
+                else reinterpret_cast<float *>(a.pop)[p] = (float)dv;
             }
         }
     }
@@ -213,8 +233,11 @@ template <int DIM> __global__ void biofilm_grow_kernel(const GrowArgs g)
                 if (g.cls[sx + (long long)g.geo.nx * (sy + (long long)g.geo.ny * sz)] & CLS_SINK) near = true;
             }
             if (near) {
-                const float C = g.c_ref + g.fld_c[g.geo.at(x, y, z)];
-                if ((double)C > g.c_thresh) {
+                // C in the lattice's arithmetic (FP32, or FP64 in the FP64 instantiation)
+                const long long k = g.geo.at(x, y, z);
+                const double C = g.dbl ? (double)g.c_ref + load_field(g.fld_c, 1, k)
+                                       : (double)(g.c_ref + reinterpret_cast<const float *>(g.fld_c)[k]);
+                if (C > g.c_thresh) {
                     const uint64_t h = splitmix64(g.seed ^ (g.cycle << 32) ^ (uint64_t)q);
                     if ((h >> 11) < g.lim) {
                         out = CLS_FLOW | CLS_SINK;

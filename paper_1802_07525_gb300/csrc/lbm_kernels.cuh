@@ -24,7 +24,8 @@
 // stores cover whole 32-byte sectors.
 //
 // Precision.  Flow populations are stored as deviations from rest (f_i - w_i), transport ones
-// as g_i - w_i c_ref; FP32 or FP16 storage, FP32 arithmetic.  The rest population of each lattice
+// as g_i - w_i c_ref; FP32 or FP16 storage with FP32 arithmetic, or FP64 storage with FP64
+// arithmetic (Arith<ST>::T).  The rest population of each lattice
 // is written as the conserved total (rho - 1, or C - kC) minus the stored moving populations, so
 // rounding cannot drift mass or substrate.  Check steps accumulate residual, mass, substrate and
 // current sums: per node and over a warp in FP32, over warps, blocks and the lattice in FP64 (one
@@ -54,6 +55,7 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     static constexpr int QF = FlowSet<DIM>::Q;
     static constexpr int QA = AdeSet<DIM, AQ>::Q;
     using LinkT = typename Links<DIM, AQ>::T;
+    using R = typename Arith<ST>::T;  // arithmetic, field and parameter type
 
     Geo geo;
     int bc[3];            // boundary kind per axis
@@ -62,27 +64,30 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     const ST *gsrc;       // transport populations, previous step, QA planes
     ST *gdst;             // transport populations, this step
     const LinkT *link;    // link mask per node
-    float *fld_rho;       // rho - 1 (written on WRITE/CHECK steps)
-    float *fld_u;         // DIM planes of velocity (read by frozen-velocity transport)
-    float *fld_c;         // C - c_ref
+    R *fld_rho;           // rho - 1 (written on WRITE/CHECK steps)
+    R *fld_u;             // DIM planes of velocity (read by frozen-velocity transport)
+    R *fld_c;             // C - c_ref
     double *partials;     // NSUM doubles per block (CHECK steps)
-    float omega;          // 1 / tau
-    float omega_c;        // 1 / tau_c
-    float k_sink;         // consumption rate
-    float u_scale;        // factor on the velocity seen by transport
-    float rho_out;        // outlet density
-    float c_ref;          // offset of the stored transport populations
+    R omega;              // 1 / tau
+    R omega_c;            // 1 / tau_c
+    R k_sink;             // consumption rate
+    R u_scale;            // factor on the velocity seen by transport
+    R rho_out;            // outlet density
+    R c_ref;              // offset of the stored transport populations
     int ade_dirichlet;    // transport outlet: 0 zero-gradient, 1 Dirichlet
-    float bb_in[QF];      // moving-wall inlet term 2 w_i rho_in (c_i . u_in) / cs^2
-    float gin_dev[QA];    // inlet ghost: w_i c_in (1 + c_i . u_in / cs^2) - w_i c_ref
-    float gout_dev[QA];   // Dirichlet outlet ghost at c_out, same form
+    R bb_in[QF];          // moving-wall inlet term 2 w_i rho_in (c_i . u_in) / cs^2
+    R gin_dev[QA];        // inlet ghost: w_i c_in (1 + c_i . u_in / cs^2) - w_i c_ref
+    R gout_dev[QA];       // Dirichlet outlet ghost at c_out, same form
 };
+
+template <typename ST> using ArithT = typename Arith<ST>::T;
 
 template <int DIM> __host__ __device__ constexpr int flow_axis() { return DIM == 2 ? 0 : 2; }
 
 // A plain (coherent) load, for values this thread stored earlier in the same kernel.
 __device__ __forceinline__ float ldplain(const float *p) { return *p; }
 __device__ __forceinline__ float ldplain(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ double ldplain(const double *p) { return *p; }
 
 template <typename T> __device__ __forceinline__ T warp_sum(T v)
 {
@@ -93,11 +98,12 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v)
 
 // Sum the NSUM per-node terms over the block; threads 0..NSUM-1 write them, as doubles, to
 // dst[0..NSUM).  Node terms and the sums over a warp and over the block (at most 256 terms)
-// are FP32; the sum over the blocks of the lattice is FP64 (finalize kernels).  GB300's FP64
-// rate is a small fraction of its FP32 rate, so per-warp FP64 work would dominate the check step.
-__device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *dst)
+// are in the arithmetic type T (FP32 except in the FP64 instantiation); the sum over the blocks
+// of the lattice is FP64 (finalize kernels).  GB300's FP64 rate is a small fraction of its FP32
+// rate, so per-warp FP64 work would dominate an FP32 check step.
+template <typename T> __device__ __forceinline__ void block_partials(T (&acc)[NSUM], double *dst)
 {
-    __shared__ float sh[8][NSUM];
+    __shared__ T sh[8][NSUM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -108,7 +114,7 @@ __device__ __forceinline__ void block_partials(float (&acc)[NSUM], double *dst)
     }
     __syncthreads();
     if (threadIdx.x < NSUM) {
-        float v = 0.f;
+        T v = 0;
         for (int w = 0; w < nwarp; ++w) v += sh[w][threadIdx.x];
         dst[threadIdx.x] = (double)v;
     }
@@ -169,8 +175,8 @@ __device__ __forceinline__ bool on_open_boundary(const Geo &g, const int (&bc)[3
 // boundary reads nothing).
 template <int DIM, typename SET, typename ST>
 __device__ __forceinline__ void ghost_images(const Geo &g, const int (&bc)[3], ST *pop, int i,
-                                             int bx, int by, int bz, bool include_zero, float v,
-                                             const ST *lazy = nullptr)
+                                             int bx, int by, int bz, bool include_zero,
+                                             ArithT<ST> v, const ST *lazy = nullptr)
 {
     const int n[3] = {g.nx, g.ny, g.nz};
     const int b[3] = {bx, by, bz};
@@ -212,21 +218,22 @@ template <int DIM, typename ST> struct LazyGhosts {
 // node's post-collision populations are read back from pop, where this thread just stored them.
 template <int DIM, typename ST, int AQ>
 __device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
-                                         long long k, uint32_t L, float u0, float u1, float u2)
+                                         long long k, uint32_t L, ArithT<ST> u0, ArithT<ST> u1, ArithT<ST> u2)
 {
+    using R = ArithT<ST>;
     using F = FlowSet<DIM>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
     const int n[3] = {a.geo.nx, a.geo.ny, a.geo.nz};
     const bool inout = a.bc[FA] == BC_INOUT;
-    const float uv[3] = {u0, u1, DIM == 3 ? u2 : 0.f};
-    const float uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+    const R uv[3] = {u0, u1, DIM == 3 ? u2 : R(0)};
+    const R uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
 #pragma unroll
     for (int i = 1; i < F::Q; ++i) {
         if (LazyGhosts<DIM, ST>::value) {
-            ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, 0.f, pop + (long long)i * a.geo.plane + k);
+            ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, R(0), pop + (long long)i * a.geo.plane + k);
         } else {
-            const float di = ldplain(pop + (long long)i * a.geo.plane + k);
+            const R di = ldplain(pop + (long long)i * a.geo.plane + k);
             ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, di);
         }
         if (!inout) continue;
@@ -237,8 +244,8 @@ __device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *
                ldplain(pop + (long long)F::opp(i) * a.geo.plane + k) + a.bb_in[i]);
         }
         if (p[FA] == n[FA] - 1 && cf == -1) {  // outlet ghost fed by this last-layer node
-            const float cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
-            const float v = F::w(i) * (a.rho_out - 1.0f +
+            const R cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
+            const R v = weight<F, R>(i) * (a.rho_out - R(1) +
                                        a.rho_out * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
             int b[3] = {x, y, z};
             b[FA] = n[FA];
@@ -253,6 +260,7 @@ template <int DIM, typename ST, int AQ>
 __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                         long long k, uint32_t L)
 {
+    using R = ArithT<ST>;
     using A = AdeSet<DIM, AQ>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
@@ -261,7 +269,7 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *p
 #pragma unroll
     for (int i = 1; i < A::Q; ++i) {
         const ST *own = pop + (long long)i * a.geo.plane + k;
-        const float ei = LazyGhosts<DIM, ST>::value ? 0.f : ldplain(own);
+        const R ei = LazyGhosts<DIM, ST>::value ? R(0) : ldplain(own);
         ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei, LazyGhosts<DIM, ST>::value ? own : nullptr);
         if (!inout) continue;
         const int cf = A::c(i, FA);
@@ -311,8 +319,9 @@ __device__ __forceinline__ bool step_writes_ghosts(const Geo &g, const int (&bc)
 // inlet/outlet axis, the outlet values from its velocity.
 template <int DIM, typename ST, int AQ>
 __device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
-                                                 long long k, float u0, float u1, float u2)
+                                                 long long k, ArithT<ST> u0, ArithT<ST> u1, ArithT<ST> u2)
 {
+    using R = ArithT<ST>;
     using F = FlowSet<DIM>;
     constexpr int FA = flow_axis<DIM>();
     const int p[3] = {x, y, z};
@@ -320,18 +329,18 @@ __device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST, AQ> &a,
     if (on_periodic_boundary<DIM>(a.geo, a.bc, x, y, z)) {
 #pragma unroll
         for (int i = 1; i < F::Q; ++i) {
-            const float di = ldplain(pop + (long long)i * a.geo.plane + k);
+            const R di = ldplain(pop + (long long)i * a.geo.plane + k);
             ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, di);
         }
     }
     if (a.bc[FA] == BC_INOUT && p[FA] == n[FA] - 1) {
-        const float uv[3] = {u0, u1, DIM == 3 ? u2 : 0.f};
-        const float uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+        const R uv[3] = {u0, u1, DIM == 3 ? u2 : R(0)};
+        const R uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
 #pragma unroll
         for (int i = 1; i < F::Q; ++i) {
             if (F::c(i, FA) != -1) continue;
-            const float cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
-            const float v = F::w(i) * (a.rho_out - 1.0f +
+            const R cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
+            const R v = weight<F, R>(i) * (a.rho_out - R(1) +
                                        a.rho_out * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
             int b[3] = {x, y, z};
             b[FA] = n[FA];
@@ -345,11 +354,12 @@ template <int DIM, typename ST, int AQ>
 __device__ __forceinline__ void ade_ghosts_step(const StepArgs<DIM, ST, AQ> &a, ST *pop, int x, int y, int z,
                                                 long long k)
 {
+    using R = ArithT<ST>;
     using A = AdeSet<DIM, AQ>;
     if (!on_periodic_boundary<DIM>(a.geo, a.bc, x, y, z)) return;
 #pragma unroll
     for (int i = 1; i < A::Q; ++i) {
-        const float ei = ldplain(pop + (long long)i * a.geo.plane + k);
+        const R ei = ldplain(pop + (long long)i * a.geo.plane + k);
         ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei);
     }
 }
@@ -369,13 +379,16 @@ __device__ __forceinline__ bool tile_on_open_boundary(const Geo &g, const int (&
 
 // Register caps of the step kernels: 2-D FP32 plain steps fit 32 registers (8 blocks of 256
 // threads per SM); 2-D FP16 plain steps (their conversions need more registers: 8% faster at 40
-// than at 32), FP32 2-D steps with D2Q9 transport, and 2-D store/check steps 40.  3-D steps are latency-bound and gain from warps:
-// FP32 with 5 blocks of 256 threads (51 registers: 148 us per 256x128x128 step, against 211 us
-// uncapped at 128 registers) and FP16 with 4 (64 registers: 154 against 178 us); tighter caps
-// spill and run slower.
+// than at 32), FP32 2-D steps with D2Q9 transport, and 2-D store/check steps 40.  3-D steps are
+// latency-bound and gain from warps: FP32 with 5 blocks of 256 threads (51 registers: 148 us per
+// 256x128x128 step, against 211 us uncapped at 128 registers) and FP16 with 4 (64 registers:
+// 154 against 178 us); tighter caps spill and run slower.  The FP64 instantiation (a parity
+// reference, twice the registers per value) gets 128.
 template <int DIM, int MODE, typename ST = float, int AQ = default_aq<DIM>()> struct StepOccupancy {
     static constexpr int blocks =
-        DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4 && AQ == 5) ? 8 : 6) : (sizeof(ST) == 4 ? 5 : 4);
+        sizeof(ST) == 8 ? 2
+                        : (DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4 && AQ == 5) ? 8 : 6)
+                                    : (sizeof(ST) == 4 ? 5 : 4));
 };
 
 // Two equivalent ways to realise the open boundaries in a step, chosen per kernel by measurement:
@@ -399,8 +412,9 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct ReaderBoundar
 // joins the reduction.  acc receives the node's check-step terms.  BFORM: the boundary form
 // (B_BOUNDARY and B_INTERIOR are for tiles that do / do not touch an open boundary).
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ>
-__device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, float (&acc)[NSUM])
+__device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, ArithT<ST> (&acc)[NSUM])
 {
+    using R = ArithT<ST>;
     static_assert(BFORM == B_WRITER || AdeSet<DIM, AQ>::Q == default_aq<DIM>(),
                   "reader-side boundaries take the transport outlet from the node itself: axis-aligned sets only");
     using F = FlowSet<DIM>;
@@ -429,10 +443,10 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     // (19 + 7 directions, 128 registers) one load per direction from an address chosen by the
     // link bit halves the load instructions and measured 4% faster.
     constexpr bool SELECT_LOADS = DIM == 3 && sizeof(ST) == 4;
-    float u[3] = {0.f, 0.f, 0.f};
+    R u[3] = {R(0), R(0), R(0)};
     // check step: the previous fields of this node (read before this thread overwrites them),
     // issued first so that their latency overlaps the population loads
-    float u_prev[3] = {0.f, 0.f, 0.f}, c_prev = 0.f;
+    R u_prev[3] = {R(0), R(0), R(0)}, c_prev = R(0);
     if (MODE == MODE_CHECK) {
         if (FLOW) {
 #pragma unroll
@@ -442,7 +456,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     }
 
     if (FLOW) {
-        float d[F::Q];
+        R d[F::Q];
 #pragma unroll
         for (int i = 0; i < F::Q; ++i) {
             const long long off = F::c(i, 0) + (long long)F::c(i, 1) * g.px + (long long)F::c(i, 2) * g.zs;
@@ -454,41 +468,41 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 d[i] = ld(a.fsrc + k + o);
                 if (F::c(i, FA) == 1 && inj) d[i] += a.bb_in[i];
             } else {
-                const float src = ld(a.fsrc + (long long)i * g.plane + k - off);
+                const R src = ld(a.fsrc + (long long)i * g.plane + k - off);
                 if (i == 0) {
                     d[0] = src;
                 } else {
-                    const float own = ld(a.fsrc + (long long)F::opp(i) * g.plane + k);
+                    const R own = ld(a.fsrc + (long long)F::opp(i) * g.plane + k);
                     d[i] = bb ? own : src;
                     if (F::c(i, FA) == 1 && inj) d[i] = own + a.bb_in[i];
                 }
             }
         }
         const bool open = !(L & (1u << LK::FLOW_SELF));
-        float rp = 0.f, j[3] = {0.f, 0.f, 0.f};
+        R rp = R(0), j[3] = {R(0), R(0), R(0)};
 #pragma unroll
         for (int i = 0; i < F::Q; ++i) {
-            if (!open) d[i] = 0.f;  // blocked nodes hold no populations
+            if (!open) d[i] = R(0);  // blocked nodes hold no populations
             rp += d[i];
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) j[ax] += F::c(i, ax) * d[i];
         }
-        const float inv = __fdividef(1.0f, 1.0f + rp);  // fast reciprocal, <= 2 ulp
-        float uu = 0.f;
+        const R inv = recip(R(1) + rp);  // FP32: fast reciprocal, <= 2 ulp
+        R uu = R(0);
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) {
             u[ax] = j[ax] * inv;
             uu += u[ax] * u[ax];
         }
         // BGK relaxation of the moving populations, then the rest one closes the mass
-        float moved = 0.f;
+        R moved = R(0);
 #pragma unroll
         for (int i = 1; i < F::Q; ++i) {
-            float cu = 0.f;
+            R cu = R(0);
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cu += F::c(i, ax) * u[ax];
-            const float feq = F::w(i) * (rp + (1.0f + rp) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-            const float v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
+            const R feq = weight<F, R>(i) * (rp + (R(1) + rp) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const R v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
             moved += v;
             if (valid) st(a.fdst + (long long)i * g.plane + k, v);
         }
@@ -499,17 +513,17 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
         }
         if (MODE != MODE_PLAIN && valid) {
             if (MODE == MODE_CHECK && open) {
-                float du2 = 0.f, u2 = 0.f;
+                R du2 = R(0), u2 = R(0);
 #pragma unroll
                 for (int ax = 0; ax < DIM; ++ax) {
-                    const float dd = u[ax] - u_prev[ax];  // exact for nearby values
+                    const R dd = u[ax] - u_prev[ax];  // exact for nearby values
                     du2 += dd * dd;
                     u2 += u[ax] * u[ax];
                 }
                 acc[SUM_DU2] = du2;
                 acc[SUM_U2] = u2;
-                acc[SUM_MASS] = 1.0f + rp;
-                if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] = 1.0f;
+                acc[SUM_MASS] = R(1) + rp;
+                if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] = R(1);
             }
             a.fld_rho[k] = rp;
 #pragma unroll
@@ -525,7 +539,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) u[ax] = a.fld_u[ax * g.plane + k] * a.u_scale;
         }
-        float e[A::Q];
+        R e[A::Q];
 #pragma unroll
         for (int i = 0; i < A::Q; ++i) {
             const long long off = A::c(i, 0) + (long long)A::c(i, 1) * g.px + (long long)A::c(i, 2) * g.zs;
@@ -539,11 +553,11 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                                        : (long long)i * g.plane - (out_v ? 0 : off);
                 e[i] = ld(a.gsrc + k + o);
             } else {
-                const float src = ld(a.gsrc + (long long)i * g.plane + k - off);
+                const R src = ld(a.gsrc + (long long)i * g.plane + k - off);
                 if (i == 0) {
                     e[0] = src;
                 } else {
-                    const float own = ld(a.gsrc + (long long)A::opp(i) * g.plane + k);
+                    const R own = ld(a.gsrc + (long long)A::opp(i) * g.plane + k);
                     e[i] = bb ? own : src;
                     if (A::c(i, FA) == -1 && out_v) e[i] = ld(a.gsrc + (long long)i * g.plane + k);
                 }
@@ -552,28 +566,28 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             if (A::c(i, FA) == -1 && out_v && a.ade_dirichlet) e[i] = a.gout_dev[i];
         }
         const bool open = !(L & (1u << LK::ADE_SELF));
-        float cp = 0.f;
+        R cp = R(0);
 #pragma unroll
         for (int i = 0; i < A::Q; ++i) {
-            if (!open) e[i] = 0.f;
+            if (!open) e[i] = R(0);
             cp += e[i];
         }
-        const float sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : 0.0f;
-        float uu_ade = 0.f;
+        const R sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : R(0);
+        R uu_ade = R(0);
         if (A::quadratic) {
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) uu_ade += u[ax] * u[ax];
         }
-        float moved = 0.f;
+        R moved = R(0);
 #pragma unroll
         for (int i = 1; i < A::Q; ++i) {
-            float cu = 0.f;
+            R cu = R(0);
 #pragma unroll
             for (int ax = 0; ax < DIM; ++ax) cu += A::c(i, ax) * u[ax];
             // linear (D2Q5 / D3Q7) or the quadratic equilibrium of Eq. 5 (D2Q9), as deviations
-            const float shape = A::quadratic ? 3.0f * cu + 4.5f * cu * cu - 1.5f * uu_ade : cu * A::inv_cs2;
-            const float geq = A::w(i) * (cp + (a.c_ref + cp) * shape);
-            const float v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - A::w(i) * sink);
+            const R shape = A::quadratic ? 3.0f * cu + 4.5f * cu * cu - 1.5f * uu_ade : cu * A::inv_cs2;
+            const R geq = weight<A, R>(i) * (cp + (a.c_ref + cp) * shape);
+            const R v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - weight<A, R>(i) * sink);
             moved += v;
             if (valid) st(a.gdst + (long long)i * g.plane + k, v);
         }
@@ -584,13 +598,13 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
         }
         if (MODE != MODE_PLAIN && valid) {
             if (MODE == MODE_CHECK && open) {
-                const float Cn = a.c_ref + cp;
-                const float dc = cp - c_prev;
+                const R Cn = a.c_ref + cp;
+                const R dc = cp - c_prev;
                 acc[SUM_DC2] = dc * dc;
                 acc[SUM_C2] = Cn * Cn;
                 acc[SUM_C] = Cn;
                 if (L & (1u << LK::SINK)) acc[SUM_CURRENT] = a.k_sink * Cn;
-                if (!isfinite(cp)) acc[SUM_BAD] += 1.0f;
+                if (!isfinite(cp)) acc[SUM_BAD] += R(1);
             }
             a.fld_c[k] = open ? cp : -a.c_ref;
         }
@@ -602,9 +616,10 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>()>
 __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
-    float acc[NSUM];
+    using R = ArithT<ST>;
+    R acc[NSUM];
 #pragma unroll
-    for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
+    for (int m = 0; m < NSUM; ++m) acc[m] = R(0);
     const int x0 = blockIdx.x * blockDim.x;
     if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
         if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, blockIdx.z))
@@ -659,9 +674,9 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 5 : StepOccupancy<DIM, MODE, S
             __syncthreads();
             cur = tile.slot;
         }
-        float acc[NSUM];
+        ArithT<ST> acc[NSUM];
 #pragma unroll
-        for (int m = 0; m < NSUM; ++m) acc[m] = 0.0f;
+        for (int m = 0; m < NSUM; ++m) acc[m] = 0;
         if (tile_on_open_boundary<DIM>(sa.geo, sa.bc, tile.x0, blockDim.x, tile.y, tile.z))
             step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(sa, tile.x0, tile.y, tile.z, acc);
         else
@@ -701,6 +716,7 @@ __device__ __forceinline__ void batch_finalize_slot(const int2 range, const doub
 template <int DIM, typename ST, int AQ = default_aq<DIM>()>
 __global__ void fill_ghosts_kernel(const StepArgs<DIM, ST, AQ> a)
 {
+    using R = ArithT<ST>;
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM, AQ>;
     using LK = Links<DIM, AQ>;
@@ -712,19 +728,19 @@ __global__ void fill_ghosts_kernel(const StepArgs<DIM, ST, AQ> a)
         const long long k = g.at(x, y, z);
         const uint32_t L = a.link[k];
         if (!(L & (1u << LK::FLOW_SELF))) {
-            float d[F::Q], rp = 0.f, j[3] = {0.f, 0.f, 0.f};
+            R d[F::Q], rp = R(0), j[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int i = 0; i < F::Q; ++i) {
                 d[i] = ld(a.fdst + (long long)i * g.plane + k);
                 rp += d[i];
                 for (int ax = 0; ax < DIM; ++ax) j[ax] += F::c(i, ax) * d[i];
             }
-            float u[3] = {0.f, 0.f, 0.f};
-            for (int ax = 0; ax < DIM; ++ax) u[ax] = j[ax] / (1.0f + rp);
+            R u[3] = {R(0), R(0), R(0)};
+            for (int ax = 0; ax < DIM; ++ax) u[ax] = j[ax] / (R(1) + rp);
             if (on_open_boundary<DIM>(g, a.bc, x, y, z)) flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, k, L, u[0], u[1], u[2]);
         }
         if (!(L & (1u << LK::ADE_SELF))) {
-            float e[A::Q];
+            R e[A::Q];
             for (int i = 0; i < A::Q; ++i) e[i] = ld(a.gdst + (long long)i * g.plane + k);
             if (on_open_boundary<DIM>(g, a.bc, x, y, z)) ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, k, L);
         }
@@ -743,7 +759,8 @@ struct MaskArgs {
     void *fpop;              // flow populations to (re)initialise: the buffer read next
     void *gpop;              // transport populations, same
     int half;                // populations stored as FP16
-    float *fld_rho, *fld_u, *fld_c;
+    int dbl;                 // populations and fields stored as FP64 (else fields are FP32)
+    void *fld_rho, *fld_u, *fld_c;
     float c_ref;
     unsigned long long *counts;  // [0] flow-open nodes, [1] transport-open nodes
 };
@@ -754,7 +771,8 @@ struct ConvArgs {
     const void *link;
     int link32;          // link words are 32-bit (3-D) or 16-bit (2-D)
     int flow_self, ade_self;
-    const float *fld_rho, *fld_u, *fld_c;
+    int dbl;             // fields stored as FP64 (else FP32)
+    const void *fld_rho, *fld_u, *fld_c;
     float c_ref;
     double *rho, *u, *c;  // dense outputs (device staging), each may be null
 };
@@ -765,9 +783,9 @@ struct PopArgs {
     const void *link;
     int link32, self_bit;
     void *pop;           // pitched deviations
-    int half;
-    float w[19];         // weights of the set
-    float offset;        // absolute = deviation + w_i * offset
+    int half, dbl;       // stored as FP16 / FP64 (else FP32)
+    double w[19];        // weights of the set (the FP32 constants, or the FP64 ones)
+    double offset;       // absolute = deviation + w_i * offset
     double *dense;       // q * N dense doubles
     int to_dense;        // 1: pop -> dense, 0: dense -> pop
 };
@@ -776,7 +794,8 @@ struct GrowArgs {
     Geo geo;
     const uint8_t *cls;   // classes before the pass
     uint8_t *cls_out;     // classes after the pass
-    const float *fld_c;   // C - c_ref (pitched)
+    const void *fld_c;    // C - c_ref (pitched)
+    int dbl;              // fld_c stored as FP64 (else FP32)
     float c_ref;
     double c_thresh;
     uint64_t seed, cycle, lim;  // convert when (h >> 11) < lim = floor(prob * 2^53)

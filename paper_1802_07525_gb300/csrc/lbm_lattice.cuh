@@ -43,6 +43,10 @@ template <> struct FlowSet<2> {
     {
         return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
     }
+    __host__ __device__ static constexpr double wd(int i)
+    {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
 };
 
 template <> struct FlowSet<3> {
@@ -63,6 +67,10 @@ template <> struct FlowSet<3> {
     {
         return i == 0 ? 1.0f / 3.0f : (i < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
     }
+    __host__ __device__ static constexpr double wd(int i)
+    {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
 };
 
 template <> struct AdeSet<2, 5> {
@@ -72,6 +80,7 @@ template <> struct AdeSet<2, 5> {
     __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<2>::c(i, a); }
     __host__ __device__ static constexpr int opp(int i) { return FlowSet<2>::opp(i); }
     __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 3.0f : 1.0f / 6.0f; }
+    __host__ __device__ static constexpr double wd(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
 };
 
 template <> struct AdeSet<3, 7> {
@@ -81,6 +90,7 @@ template <> struct AdeSet<3, 7> {
     __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<3>::c(i, a); }
     __host__ __device__ static constexpr int opp(int i) { return FlowSet<3>::opp(i); }
     __host__ __device__ static constexpr float w(int i) { return i == 0 ? 1.0f / 4.0f : 1.0f / 8.0f; }
+    __host__ __device__ static constexpr double wd(int i) { return i == 0 ? 1.0 / 4.0 : 1.0 / 8.0; }
 };
 
 // D2Q9 transport with the flow equilibrium of Eq. 5 (C in place of rho):
@@ -92,7 +102,15 @@ template <> struct AdeSet<2, 9> {
     __host__ __device__ static constexpr int c(int i, int a) { return FlowSet<2>::c(i, a); }
     __host__ __device__ static constexpr int opp(int i) { return FlowSet<2>::opp(i); }
     __host__ __device__ static constexpr float w(int i) { return FlowSet<2>::w(i); }
+    __host__ __device__ static constexpr double wd(int i) { return FlowSet<2>::wd(i); }
 };
+
+// Weight w_i of a velocity set in the arithmetic type R: the FP32 constants in FP32 arithmetic,
+// the rationals rounded once to double in FP64 arithmetic.
+template <typename SET, typename R> __host__ __device__ constexpr R weight(int i)
+{
+    return std::is_same<R, double>::value ? (R)SET::wd(i) : (R)SET::w(i);
+}
 
 // ---- link masks ------------------------------------------------------------------------------
 // One word per node.  Bit 0: the node is blocked for the flow.  Bit i (1..Qf-1): the flow
@@ -109,14 +127,29 @@ template <int DIM, int AQ = default_aq<DIM>()> struct Links {
 };
 
 // ---- storage ---------------------------------------------------------------------------------
-// Populations are stored as deviations from the rest state in FP32 or FP16; arithmetic is FP32.
+// Populations are stored as deviations from the rest state in FP32 or FP16 with FP32
+// arithmetic, or in FP64 with FP64 arithmetic (the double-precision instantiation of the same
+// kernels, for parity with the FP64 reference at rounding level).  Arith<ST>::T is the type of
+// the arithmetic, of the fields (rho - 1, u, C - c_ref) and of the per-node check-step terms.
+template <typename ST> struct Arith {
+    using T = float;
+};
+template <> struct Arith<double> {
+    using T = double;
+};
 __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
-// The value a store of v keeps (identity in FP32, rounded to FP16 in FP16 storage).
+__device__ __forceinline__ void st(double *p, double v) { *p = v; }
+// The value a store of v keeps (identity in FP32 and FP64, rounded to FP16 in FP16 storage).
 __device__ __forceinline__ float kept(const float *, float v) { return v; }
 __device__ __forceinline__ float kept(const __half *, float v) { return __half2float(__float2half_rn(v)); }
+__device__ __forceinline__ double kept(const double *, double v) { return v; }
+// 1 / x: the fast FP32 reciprocal-division (at most 2 ulp) in FP32, IEEE division in FP64.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Sums produced by a residual-check step (one double each, per block then per lattice).
 enum : int {

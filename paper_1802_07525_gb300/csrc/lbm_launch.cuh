@@ -1,5 +1,6 @@
 // Launchers of the step, batch-step and ghost-fill kernels for one dimension (MFC_DIM), one
-// storage type (MFC_ST) and one transport velocity set (MFC_AQ, default D2Q5 / D3Q7), included
+// storage type (MFC_ST: float, __half, or double for the FP64 instantiation) and one transport
+// velocity set (MFC_AQ, default D2Q5 / D3Q7), included
 // by one translation unit per combination so that the instantiations compile in parallel.  The
 // batch launchers exist for the default transport sets only (MFC_BATCH_FN defined).
 #include <string.h>
@@ -45,14 +46,17 @@ Args make_args(const StepHost &h)
     a.gsrc = static_cast<const ST *>(h.gsrc);
     a.gdst = static_cast<ST *>(h.gdst);
     a.link = static_cast<const typename Links<D, AQ>::T *>(h.link);
-    a.fld_rho = h.fld_rho; a.fld_u = h.fld_u; a.fld_c = h.fld_c;
+    using R = typename Args::R;
+    a.fld_rho = static_cast<R *>(h.fld_rho);
+    a.fld_u = static_cast<R *>(h.fld_u);
+    a.fld_c = static_cast<R *>(h.fld_c);
     a.partials = h.partials;
-    a.omega = h.omega; a.omega_c = h.omega_c; a.k_sink = h.k_sink; a.u_scale = h.u_scale;
-    a.rho_out = h.rho_out; a.c_ref = h.c_ref; a.ade_dirichlet = h.ade_dirichlet;
-    for (int i = 0; i < Args::QF; ++i) a.bb_in[i] = h.bb_in[i];
+    a.omega = (R)h.omega; a.omega_c = (R)h.omega_c; a.k_sink = (R)h.k_sink; a.u_scale = (R)h.u_scale;
+    a.rho_out = (R)h.rho_out; a.c_ref = (R)h.c_ref; a.ade_dirichlet = h.ade_dirichlet;
+    for (int i = 0; i < Args::QF; ++i) a.bb_in[i] = (R)h.bb_in[i];
     for (int i = 0; i < Args::QA; ++i) {
-        a.gin_dev[i] = h.gin_dev[i];
-        a.gout_dev[i] = h.gout_dev[i];
+        a.gin_dev[i] = (R)h.gin_dev[i];
+        a.gout_dev[i] = (R)h.gout_dev[i];
     }
     return a;
 }

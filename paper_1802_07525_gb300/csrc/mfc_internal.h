@@ -16,6 +16,7 @@ enum : int { DEFAULT_BLOCK = 128 };
 // Everything a step launch needs, independent of dimension and storage type.
 struct StepHost {
     int dim, half;
+    int dbl;  // FP64 storage and arithmetic (the double-precision instantiation)
     int aq;  // transport velocity set: 5 / 7 (default) or 9 (D2Q9, 2-D)
     int kind, mode;
     Geo geo;
@@ -27,11 +28,12 @@ struct StepHost {
     const void *gsrc;
     void *gdst;
     const void *link;
-    float *fld_rho, *fld_u, *fld_c;
+    void *fld_rho, *fld_u, *fld_c;  // fields in the arithmetic type (FP32, or FP64 when dbl)
     double *partials;
-    float omega, omega_c, k_sink, u_scale, rho_out, c_ref;
+    // parameters in double; the argument block holds them in the arithmetic type
+    double omega, omega_c, k_sink, u_scale, rho_out, c_ref;
     int ade_dirichlet;
-    float bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
+    double bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
 };
 
 // One launch of the batch step kernel over a tile table (coupled steps).
@@ -58,6 +60,13 @@ cudaError_t launch_step_2d9_f32(StepHost &h, cudaStream_t s);
 cudaError_t launch_step_2d9_f16(StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_2d9_f32(const StepHost &h, cudaStream_t s);
 cudaError_t launch_fill_ghosts_2d9_f16(const StepHost &h, cudaStream_t s);
+// The FP64 instantiation (parity reference; single lattices only)
+cudaError_t launch_step_2d_f64(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_3d_f64(StepHost &h, cudaStream_t s);
+cudaError_t launch_step_2d9_f64(StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d_f64(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_3d_f64(const StepHost &h, cudaStream_t s);
+cudaError_t launch_fill_ghosts_2d9_f64(const StepHost &h, cudaStream_t s);
 
 cudaError_t launch_batch_2d_f32(const BatchHost &h, cudaStream_t s);
 cudaError_t launch_batch_2d_f16(const BatchHost &h, cudaStream_t s);
@@ -95,6 +104,7 @@ inline size_t step_args(const StepHost &h, void *out)
 
 inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
 {
+    if (h.dbl) return h.dim == 3 ? launch_step_3d_f64(h, s) : (h.aq == 9 ? launch_step_2d9_f64(h, s) : launch_step_2d_f64(h, s));
     if (h.dim == 2 && h.aq == 9) return h.half ? launch_step_2d9_f16(h, s) : launch_step_2d9_f32(h, s);
     if (h.dim == 2) return h.half ? launch_step_2d_f16(h, s) : launch_step_2d_f32(h, s);
     return h.half ? launch_step_3d_f16(h, s) : launch_step_3d_f32(h, s);
@@ -102,6 +112,9 @@ inline cudaError_t launch_step(StepHost &h, cudaStream_t s)
 
 inline cudaError_t launch_fill_ghosts(const StepHost &h, cudaStream_t s)
 {
+    if (h.dbl)
+        return h.dim == 3 ? launch_fill_ghosts_3d_f64(h, s)
+                          : (h.aq == 9 ? launch_fill_ghosts_2d9_f64(h, s) : launch_fill_ghosts_2d_f64(h, s));
     if (h.dim == 2 && h.aq == 9) return h.half ? launch_fill_ghosts_2d9_f16(h, s) : launch_fill_ghosts_2d9_f32(h, s);
     if (h.dim == 2) return h.half ? launch_fill_ghosts_2d_f16(h, s) : launch_fill_ghosts_2d_f32(h, s);
     return h.half ? launch_fill_ghosts_3d_f16(h, s) : launch_fill_ghosts_3d_f32(h, s);

@@ -159,8 +159,8 @@ mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
             return MFC_ERR_ARG;
         }
     }
-    if (d->precision != MFC_FP32 && d->precision != MFC_FP16_DEV) {
-        *why = "precision must be MFC_FP32 or MFC_FP16_DEV";
+    if (d->precision != MFC_FP32 && d->precision != MFC_FP16_DEV && d->precision != MFC_FP64) {
+        *why = "precision must be MFC_FP32, MFC_FP16_DEV or MFC_FP64";
         return MFC_ERR_ARG;
     }
     if (!(d->ade_q == 0 || (d->dim == 2 && (d->ade_q == 5 || d->ade_q == 9)) || (d->dim == 3 && d->ade_q == 7))) {
@@ -175,6 +175,7 @@ struct Layout {
     Geo geo;
     long long N;
     size_t st, link_bytes;
+    size_t fb;  // bytes per field value: 4, or 8 in the FP64 instantiation
 };
 
 // Ghost-layer layout: row pitch px = nx + 2 rounded up to 4 (left ghost of a row in the padding
@@ -198,7 +199,8 @@ Layout layout_of(const mfc_lattice_desc *d)
     const long long last = g.at(0, g.ny + 1, g.nz - 1 + gz);  // first element past the last ghost row
     g.plane = (long long)round_up((size_t)(last + 2 * g.px + 64), 64);
     l.N = (long long)g.nx * g.ny * g.nz;
-    l.st = d->precision == MFC_FP16_DEV ? 2 : 4;
+    l.st = d->precision == MFC_FP16_DEV ? 2 : (d->precision == MFC_FP64 ? 8 : 4);
+    l.fb = d->precision == MFC_FP64 ? 8 : 4;
     l.link_bytes = (d->dim == 2 && l.qa == 5) ? 2 : 4;  // 9 + 9 + 1 link bits need 32-bit words
     return l;
 }
@@ -223,6 +225,7 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     memset(h, 0, sizeof *h);
     h->dim = L->dim;
     h->half = L->half;
+    h->dbl = L->dbl;
     h->kind = kind;
     h->mode = mode;
     h->geo = L->geo;
@@ -238,18 +241,22 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->fld_rho = L->fld_rho; h->fld_u = L->fld_u; h->fld_c = L->fld_c;
     h->partials = L->partials;
     const mfc_params &p = L->prm;
-    h->omega = (float)(1.0 / p.tau);
-    h->omega_c = (float)(1.0 / p.tau_c);
-    h->k_sink = (float)p.k_sink;
-    h->u_scale = (float)p.u_scale;
-    h->rho_out = (float)p.rho_out;
+    // Parameters are kept in double here and rounded once to the arithmetic type when the
+    // argument block is built; the weights are that type's (FP32 constants, or FP64 ones).
+    const bool dbl = L->dbl;
+    h->omega = 1.0 / p.tau;
+    h->omega_c = 1.0 / p.tau_c;
+    h->k_sink = p.k_sink;
+    h->u_scale = p.u_scale;
+    h->rho_out = p.rho_out;
     h->c_ref = L->c_ref;
     h->ade_dirichlet = p.ade_outlet == MFC_OUTLET_DIRICHLET;
     const int fa = L->dim == 2 ? 0 : 2;
     for (int i = 0; i < L->qf; ++i) {
         const int ci = L->dim == 2 ? FlowSet<2>::c(i, fa) : FlowSet<3>::c(i, fa);
-        const double w = L->dim == 2 ? FlowSet<2>::w(i) : FlowSet<3>::w(i);
-        h->bb_in[i] = (float)(2.0 * w * p.rho_in * ci * p.u_in * 3.0);
+        const double w = L->dim == 2 ? (dbl ? FlowSet<2>::wd(i) : FlowSet<2>::w(i))
+                                     : (dbl ? FlowSet<3>::wd(i) : FlowSet<3>::w(i));
+        h->bb_in[i] = 2.0 * w * p.rho_in * ci * p.u_in * 3.0;
     }
     // transport inlet (and Dirichlet outlet) equilibria at the inlet velocity: linear on D2Q5 /
     // D3Q7, the quadratic form of Eq. 5 on D2Q9
@@ -259,16 +266,16 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
         double w, shape;
         if (L->qa == 9) {
             ci = AdeSet<2, 9>::c(i, fa);
-            w = AdeSet<2, 9>::w(i);
+            w = dbl ? AdeSet<2, 9>::wd(i) : AdeSet<2, 9>::w(i);
             const double cu = ci * p.u_in;
             shape = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * p.u_in * p.u_in;
         } else {
             ci = L->dim == 2 ? AdeSet<2>::c(i, fa) : AdeSet<3>::c(i, fa);
-            w = L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i);
+            w = L->dim == 2 ? (dbl ? AdeSet<2>::wd(i) : AdeSet<2>::w(i)) : (dbl ? AdeSet<3>::wd(i) : AdeSet<3>::w(i));
             shape = 1.0 + ci * p.u_in * inv_cs2;
         }
-        h->gin_dev[i] = (float)(w * p.c_in * shape - w * L->c_ref);
-        h->gout_dev[i] = (float)(w * p.c_out * shape - w * L->c_ref);
+        h->gin_dev[i] = w * p.c_in * shape - w * L->c_ref;
+        h->gout_dev[i] = w * p.c_out * shape - w * L->c_ref;
     }
     h->aq = L->qa;
 }
@@ -519,6 +526,7 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
     m.fpop = L->f[L->fcur];
     m.gpop = L->g[L->gcur];
     m.half = L->half;
+    m.dbl = L->dbl;
     m.fld_rho = L->fld_rho; m.fld_u = L->fld_u; m.fld_c = L->fld_c;
     m.c_ref = L->c_ref;
     m.counts = L->counts_d;
@@ -575,6 +583,7 @@ mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *p
     L->N = l.N;
     L->st_bytes = l.st;
     L->half = desc->precision == MFC_FP16_DEV;
+    L->dbl = desc->precision == MFC_FP64;
     L->link32 = l.link_bytes == 4;
     // transport storage offset: 0, so that the no-substrate start state is stored exactly
     L->c_ref = 0.0f;
@@ -611,9 +620,9 @@ mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *p
     ok = ok && dalloc(&L->link, (size_t)P * l.link_bytes);
     ok = ok && dalloc((void **)&L->cls_cur, round_up((size_t)l.N, 256));
     ok = ok && dalloc((void **)&L->cls_tmp, round_up((size_t)l.N, 256));
-    ok = ok && dalloc((void **)&L->fld_rho, (size_t)P * 4);
-    ok = ok && dalloc((void **)&L->fld_u, (size_t)l.dim * P * 4);
-    ok = ok && dalloc((void **)&L->fld_c, (size_t)P * 4);
+    ok = ok && dalloc(&L->fld_rho, (size_t)P * l.fb);
+    ok = ok && dalloc(&L->fld_u, (size_t)l.dim * P * l.fb);
+    ok = ok && dalloc(&L->fld_c, (size_t)P * l.fb);
     // per-block partials, then the stage-1 sums of the finalize
     ok = ok && dalloc((void **)&L->partials, ((size_t)L->max_blocks + FINAL_STAGE1_MAX) * NSUM * sizeof(double));
     ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
@@ -673,7 +682,7 @@ MFC_API size_t mfc_lattice_bytes(const mfc_lattice_desc *desc)
     b += 2 * (size_t)l.qa * P * l.st;             // transport A/B
     b += (size_t)P * l.link_bytes;                // links
     b += 2 * round_up((size_t)l.N, 256);          // classes (current, next)
-    b += (size_t)(2 + l.dim) * P * 4;             // fields
+    b += (size_t)(2 + l.dim) * P * l.fb;          // fields
     b += ((size_t)max_launch_blocks(l) + FINAL_STAGE1_MAX) * NSUM * sizeof(double);  // partials
     b += 4096;
     return b;
@@ -789,6 +798,7 @@ MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *L, uint64_t seed, uint64_t cycl
     g.cls = L->cls_cur;
     g.cls_out = L->cls_tmp;
     g.fld_c = L->fld_c;
+    g.dbl = L->dbl;
     g.c_ref = L->c_ref;
     g.c_thresh = c_thresh;
     g.seed = seed;
@@ -822,6 +832,7 @@ MFC_API mfc_status mfc_read_fields(mfc_lattice *L, double *rho, double *u, doubl
     a.link32 = L->link32;
     a.flow_self = 0;
     a.ade_self = L->qf;
+    a.dbl = L->dbl;
     a.fld_rho = L->fld_rho; a.fld_u = L->fld_u; a.fld_c = L->fld_c;
     a.c_ref = L->c_ref;
     a.rho = rho ? L->staging : nullptr;
@@ -852,21 +863,28 @@ static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const doub
         a.q = L->qf;
         a.pop = L->f[L->fcur];
         a.half = L->half;
+        a.dbl = L->dbl;
         a.self_bit = 0;
-        a.offset = 1.0f;
-        for (int i = 0; i < a.q; ++i) a.w[i] = L->dim == 2 ? FlowSet<2>::w(i) : FlowSet<3>::w(i);
+        a.offset = 1.0;
+        for (int i = 0; i < a.q; ++i)
+            a.w[i] = L->dim == 2 ? (L->dbl ? FlowSet<2>::wd(i) : FlowSet<2>::w(i))
+                                 : (L->dbl ? FlowSet<3>::wd(i) : FlowSet<3>::w(i));
     } else if (which == MFC_POP_ADE) {
         a.q = L->qa;
         a.pop = L->g[L->gcur];
         a.half = L->half;
+        a.dbl = L->dbl;
         a.self_bit = L->qf;
         a.offset = L->c_ref;
-        for (int i = 0; i < a.q; ++i)
-            a.w[i] = L->qa == 9 ? AdeSet<2, 9>::w(i) : (L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i));
+        for (int i = 0; i < a.q; ++i) {
+            if (L->dbl) a.w[i] = L->qa == 9 ? AdeSet<2, 9>::wd(i) : (L->dim == 2 ? AdeSet<2>::wd(i) : AdeSet<3>::wd(i));
+            else a.w[i] = L->qa == 9 ? AdeSet<2, 9>::w(i) : (L->dim == 2 ? AdeSet<2>::w(i) : AdeSet<3>::w(i));
+        }
     } else if (which == MFC_FIELD_VELOCITY) {
         a.q = L->dim;
         a.pop = L->fld_u;
         a.half = 0;
+        a.dbl = L->dbl;
         a.self_bit = host_out ? 0 : -1;
         a.offset = 0.0f;
     } else {

@@ -23,6 +23,7 @@ struct mfc_lattice {
     mfc_lattice_desc desc;
     mfc_params prm;
     int dim = 2, qf = 9, qa = 5, half = 0;
+    int dbl = 0;  // FP64 storage, arithmetic and fields (MFC_FP64)
     int nx = 1, ny = 1, nz = 1;
     mfc::Geo geo;
     long long N = 0;
@@ -38,7 +39,8 @@ struct mfc_lattice {
     void *link = nullptr;
     int link32 = 0;
     uint8_t *cls_cur = nullptr, *cls_tmp = nullptr;
-    float *fld_rho = nullptr, *fld_u = nullptr, *fld_c = nullptr;
+    // fields (rho - 1, u, C - c_ref): FP32, or FP64 in the FP64 instantiation (dbl)
+    void *fld_rho = nullptr, *fld_u = nullptr, *fld_c = nullptr;
     double *partials = nullptr;
     double *results_d = nullptr, *results_h = nullptr;
     unsigned long long *counts_d = nullptr, *counts_h = nullptr;

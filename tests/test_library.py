@@ -59,6 +59,19 @@ def test_host_only_calls(libpath):
     assert b16 < b2
     b3 = mfc.lattice_bytes((64, 32, 48))
     assert b3 >= 2 * 26 * 4 * 64 * 32 * 48
+    # FP64 storage: populations at 8 B and fields at 8 B.  The FP32 - FP16 difference gives the
+    # plane size P (2 buffers x 14 planes x 2 B per element), from which the FP64 - FP32
+    # difference is fixed: 2 x 14 planes x 4 B more, and 2 + dim fields x 4 B more.
+    b64 = mfc.lattice_bytes((2048, 1024), precision=mfc.MFC_FP64)
+    P = (b2 - b16) // (2 * 14 * 2)
+    assert (b2 - b16) % (2 * 14 * 2) == 0 and P >= 2048 * 1024
+    assert b64 - b2 == 2 * 14 * P * 4 + (2 + 2) * P * 4
+    assert mfc.lattice_bytes((2048, 1024), precision=3) == 0
+    # batches take FP32 or FP16 storage only; refused before any device call
+    import pytest
+    with pytest.raises(mfc.MfcError) as e:
+        mfc.Batch(precision=mfc.MFC_FP64)
+    assert e.value.status == mfc.MFC_ERR_ARG
     # invalid descriptors are refused without touching a device
     assert mfc.lattice_bytes((0, 4)) == 0
     assert mfc.lattice_bytes((8, 8), bc=(mfc.MFC_BC_WALL, mfc.MFC_BC_INOUT)) == 0
