@@ -439,10 +439,11 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     const bool at_in = inout && pf == 0;
     const bool at_out = inout && pf == (FA == 0 ? g.nx : g.nz) - 1;
     // How a bounce-back population is fetched.  Unconditional own-opposite loads, selected
-    // afterwards, keep every load independent of the link word (2-D, and FP16 3-D); in FP32 3-D
-    // (19 + 7 directions, 128 registers) one load per direction from an address chosen by the
-    // link bit halves the load instructions and measured 4% faster.
-    constexpr bool SELECT_LOADS = DIM == 3 && sizeof(ST) == 4;
+    // afterwards, keep every load independent of the link word (2-D: measured faster in FP32
+    // and FP16); in 3-D (19 + 7 directions under tight register caps) one load per direction from
+    // an address chosen by the link bit halves the load instructions and measured 4% (FP32) and
+    // 3% (FP16) faster.
+    constexpr bool SELECT_LOADS = DIM == 3;
     R u[3] = {R(0), R(0), R(0)};
     // check step: the previous fields of this node (read before this thread overwrites them),
     // issued first so that their latency overlaps the population loads
@@ -621,13 +622,17 @@ __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks)
 #pragma unroll
     for (int m = 0; m < NSUM; ++m) acc[m] = R(0);
     const int x0 = blockIdx.x * blockDim.x;
+    // 3-D: the last plane first (blocks are dispatched in z order), so that the outlet plane's
+    // ghost work overlaps the bulk of the step instead of lengthening its tail (1.5% faster on
+    // 256x128x128); 2-D keeps row order, whose locality is worth more.
+    const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
-        if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, blockIdx.z))
-            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(a, x0, blockIdx.y, blockIdx.z, acc);
+        if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, z))
+            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(a, x0, blockIdx.y, z, acc);
         else
-            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR>(a, x0, blockIdx.y, blockIdx.z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR>(a, x0, blockIdx.y, z, acc);
     } else {
-        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER>(a, x0, blockIdx.y, blockIdx.z, acc);
+        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER>(a, x0, blockIdx.y, z, acc);
     }
     if (MODE == MODE_CHECK)
         block_partials(acc, a.partials + ((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y *
