@@ -266,10 +266,18 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *p
     const int p[3] = {x, y, z};
     const int n[3] = {a.geo.nx, a.geo.ny, a.geo.nz};
     const bool inout = a.bc[FA] == BC_INOUT;
+    // Eager form: every read-back is issued before the first ghost store, so the loads overlap
+    // (a load placed after a store that may alias it cannot be moved ahead of it).  Measured on
+    // the FP32 2-D step: 42.8 against 44.5 us per 2048x1024 step.  The same change in
+    // flow_ghosts spills at 32 registers and runs slower.
+    R ev[A::Q];
+#pragma unroll
+    for (int i = 1; i < A::Q; ++i)
+        ev[i] = LazyGhosts<DIM, ST>::value ? R(0) : ldplain(pop + (long long)i * a.geo.plane + k);
 #pragma unroll
     for (int i = 1; i < A::Q; ++i) {
         const ST *own = pop + (long long)i * a.geo.plane + k;
-        const R ei = LazyGhosts<DIM, ST>::value ? R(0) : ldplain(own);
+        const R ei = ev[i];
         ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei, LazyGhosts<DIM, ST>::value ? own : nullptr);
         if (!inout) continue;
         const int cf = A::c(i, FA);
