@@ -256,7 +256,7 @@ typedef struct mfc_batch mfc_batch; /* opaque */
 
 typedef struct {
     size_t budget_bytes;  /* device memory for instances; 0 = 90% of the free memory at create */
-    int precision;        /* MFC_FP32 or MFC_FP16_DEV, for every instance */
+    int precision;        /* MFC_FP32 or MFC_FP16_DEV, for every instance (MFC_FP64: MFC_ERR_ARG) */
     int check_every;      /* K (even, >= 2; odd values are rounded up); 0 = chosen by the autotuner */
     int block;            /* threads per tile: 64, 128 or 256; 0 = chosen by the autotuner */
     int max_instances;    /* instance slots, 1..4096; 0 = 256 */
