@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("tau_c", ctypes.c_double), ("u_in", ctypes.c_double),
         ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double), ("c_in", ctypes.c_double),
         ("c_out", ctypes.c_double),
-        ("k_sink", ctypes.c_double), ("u_scale", ctypes.c_double),
+        ("k_sink", ctypes.c_double), ("u_scale", ctypes.c_double), ("k_half", ctypes.c_double),
     ]
 
 
@@ -138,7 +138,7 @@ class Oracle:
 
     def __init__(self, shape, cls=None, *, bc=None, ade_q=None,
                  ade_outlet=0, tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0, c_out=0.0,
-                 k_sink=1e-3, u_scale=1.0):
+                 k_sink=1e-3, u_scale=1.0, k_half=0.0):
         shape = tuple(int(s) for s in shape)
         self.dim = len(shape)
         nx, ny = shape[0], shape[1]
@@ -158,7 +158,7 @@ class Oracle:
             p.bc[a] = bcs[a]
         p.ade_q, p.ade_outlet = self.qa, ade_outlet
         p.tau, p.tau_c, p.u_in, p.rho_in, p.rho_out = tau, tau_c, u_in, rho_in, rho_out
-        p.c_in, p.c_out, p.k_sink, p.u_scale = c_in, c_out, k_sink, u_scale
+        p.c_in, p.c_out, p.k_sink, p.u_scale, p.k_half = c_in, c_out, k_sink, u_scale, k_half
         self.p = p
         if cls is None:
             cls = np.zeros(self.N, np.uint8)

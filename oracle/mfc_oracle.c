@@ -47,7 +47,19 @@ typedef struct {
     double c_out;      /* outlet concentration when ade_outlet = 1 */
     double k_sink;     /* first-order consumption rate on sink nodes */
     double u_scale;    /* factor applied to the flow velocity seen by the transport solver */
+    double k_half;     /* half-saturation concentration K_s of the substrate factor of Eq. 16;
+                          0 = the first-order limit k*C */
 } orc_params;
+
+/* Consumption on a sink node at concentration C (Eq. 16, substrate factor): the saturating
+ * rate q_max C / (C + K_s) with q_max = k_sink K_s, so that k_sink is the rate per unit
+ * concentration at low C; K_s = 0 selects the first-order limit k_sink C.  The mediator factor
+ * M_ox / (M_ox + K_Mox) is taken as constant and folded into k_sink. */
+static double consumption(const orc_params *p, double C)
+{
+    if (p->k_half > 0.0) return p->k_sink * p->k_half * C / (p->k_half + C);
+    return p->k_sink * C;
+}
 
 /* ------------------------------------------------------------------------------------------
  * Velocity sets.
@@ -303,9 +315,9 @@ ORC_API void orc_flow_step(const orc_params *p, const uint8_t *cls, const double
  * The velocity u (dim x N) is held fixed during the transport solve (text after Eq. 12); it
  * is scaled by u_scale and taken as zero on nodes blocked for the flow (biofilm is
  * impermeable to flow, Sec. 3.3, but still takes part in transport).
- * Consumption: the first-order rate k*C on sink nodes, removed in proportion to the weights,
- * so that sum_i G_i loses exactly k*C per sink node per step.  Eq. 12 prints no source term;
- * the consumption follows the substrate uptake of Eq. 16 in its first-order limit.
+ * Consumption: the rate of consumption() on sink nodes (first order k*C, or the saturating
+ * substrate factor of Eq. 16), removed in proportion to the weights, so that sum_i G_i loses
+ * exactly that rate per sink node per step.  Eq. 12 prints no source term.
  * Out: gn (0 on blocked nodes) and conc = moment of the streamed populations (Eq. 13). */
 ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double *g, double *gn,
                           const double *u, double *conc)
@@ -345,7 +357,7 @@ ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double 
                 for (int i = 0; i < v.q; ++i) C += gin[i];
                 double geq[19];
                 ade_equilibrium(&v, C, uk, geq);
-                double sink = (cls[k] & CLS_SINK) ? p->k_sink * C : 0.0;
+                double sink = (cls[k] & CLS_SINK) ? consumption(p, C) : 0.0;
                 for (int i = 0; i < v.q; ++i)
                     gn[i * N + k] = gin[i] - (gin[i] - geq[i]) / p->tau_c - v.w[i] * sink;
                 conc[k] = C;
@@ -355,7 +367,8 @@ ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double 
 /* Global sums used by the steady-state test and the current (FP64).
  * out[0] = sum |u - u_prev|^2, out[1] = sum |u|^2, out[2] = sum rho      (flow-active nodes)
  * out[3] = sum (C - C_prev)^2, out[4] = sum C^2,  out[5] = sum C        (transport-active)
- * out[6] = sum over sink nodes of k*C  (the consumption that sets the current, Eqs. 16, 20)
+ * out[6] = sum over sink nodes of the consumption (the substrate uptake that sets the current,
+ *          Eqs. 16, 20)
  * out[7] = number of non-finite values met. */
 ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho, const double *u,
                       const double *u_prev, const double *conc, const double *conc_prev,
@@ -379,7 +392,7 @@ ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho
             out[3] += d * d;
             out[4] += conc[k] * conc[k];
             out[5] += conc[k];
-            if (cls[k] & CLS_SINK) out[6] += p->k_sink * conc[k];
+            if (cls[k] & CLS_SINK) out[6] += consumption(p, conc[k]);
             if (!isfinite(conc[k])) out[7] += 1.0;
         }
     }

@@ -405,16 +405,67 @@ def test_uniform_sink_decays_geometrically(dim):
         assert s[6] == pytest.approx(N * k_sink * expect, rel=1e-13)
 
 
-def test_substrate_balance_closed_box():
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("K,C0", [(5.0, 0.1), (0.4, 0.4), (0.02, 0.4)])
+def test_uniform_monod_sink_follows_the_scalar_map(dim, K, C0):
+    """Eq. 16's substrate factor on every node, no flow: a uniform state stays uniform, and
+    its concentration follows the scalar map C <- C - k K C / (K + C), iterated here on its own,
+    from well below K (near first order) to far above it (near zero order); the current is
+    N k K C / (K + C)."""
+    shape = (8, 6) if dim == 2 else (4, 3, 5)
+    N = int(np.prod(shape))
+    k = 0.1
+    o = oracle.Oracle(shape, np.full(N, SINK, np.uint8), bc=(BC_PERIODIC,) * 3, k_sink=k,
+                      k_half=K, tau_c=0.9)
+    o.g[:] = oracle.ade_equilibrium(o.qa, C0, [0.0] * dim)[:, None]
+    uu = np.zeros((dim, N))
+    c = C0
+    for t in range(1, 30):
+        o.step_ade(1, u=uu)
+        assert np.allclose(o.conc, c, rtol=1e-13, atol=0), t
+        assert o.sums()[6] == pytest.approx(N * k * K * c / (K + c), rel=1e-13)
+        c = c - k * K * c / (K + c)
+
+
+def test_monod_sink_limits():
+    """Saturated (C >> K): each step removes k K C / (K + C), between k K - k K^2 / (K + C)
+    and k K, so the concentration falls linearly: C^t lies above C0 - (t - 1) k K, and by at
+    most (t - 1) k K^2 / (K + C).
+    K -> infinity: the first-order sink k C (geometric decay)."""
+    shape = (6, 5)
+    N = 30
+    k, K, C0 = 0.2, 1e-3, 1.0
+    o = oracle.Oracle(shape, np.full(N, SINK, np.uint8), bc=(BC_PERIODIC,) * 3, k_sink=k,
+                      k_half=K, tau_c=0.8)
+    o.g[:] = oracle.ade_equilibrium(5, C0, [0.0, 0.0])[:, None]
+    uu = np.zeros((2, N))
+    for t in range(1, 40):
+        o.step_ade(1, u=uu)
+        lin = C0 - (t - 1) * k * K
+        # each step removes less than k K, and more than k K - k K^2 / (K + C); 1e-15 allows
+        # for the rounding of the moment of the stored populations
+        assert o.conc.min() >= lin - 1e-15
+        assert o.conc.max() - lin <= (t - 1) * k * K * K / (K + o.conc.min()) + 1e-15
+    big = oracle.Oracle(shape, np.full(N, SINK, np.uint8), bc=(BC_PERIODIC,) * 3, k_sink=k,
+                        k_half=1e15, tau_c=0.8)
+    big.g[:] = oracle.ade_equilibrium(5, C0, [0.0, 0.0])[:, None]
+    for t in range(1, 20):
+        big.step_ade(1, u=uu)
+        assert np.allclose(big.conc, C0 * (1 - k) ** (t - 1), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("k_half", [0.0, 0.3])
+def test_substrate_balance_closed_box(k_half):
     """Closed box with obstacles, sinks and an arbitrary frozen velocity: each step the total
-    substrate falls by exactly the consumption, sum C^(t+1) = sum C^t - I^t."""
+    substrate falls by exactly the consumption, sum C^(t+1) = sum C^t - I^t (first-order and
+    saturating consumption)."""
     shape = (14, 11)
     N = 154
     rng = np.random.default_rng(9)
     r = rng.random(N)
     cls = np.where(r < 0.15, FLOW_SOLID | ADE_SOLID, np.where(r < 0.35, SINK, 0)).astype(np.uint8)
     cls[(r > 0.9)] = FLOW_SOLID | SINK
-    o = oracle.Oracle(shape, cls, bc=(BC_WALL, BC_WALL), k_sink=0.05, tau_c=0.65)
+    o = oracle.Oracle(shape, cls, bc=(BC_WALL, BC_WALL), k_sink=0.05, tau_c=0.65, k_half=k_half)
     o.g[:] = rng.random(o.g.shape)
     o.g[:, (cls & ADE_SOLID) > 0] = 0.0
     uu = 0.05 * rng.standard_normal((2, N))
@@ -426,7 +477,8 @@ def test_substrate_balance_closed_box():
         assert s[5] == pytest.approx(s_prev[5] - s_prev[6], rel=1e-13)
 
 
-def test_substrate_balance_channel_fluxes():
+@pytest.mark.parametrize("k_half", [0.0, 0.1])
+def test_substrate_balance_channel_fluxes(k_half):
     """Open channel (D2Q5): the change of total substrate equals inlet inflow minus what
     leaves through the inlet and outlet planes plus what the zero-gradient outlet returns,
     minus the consumption, to round-off."""
@@ -439,7 +491,7 @@ def test_substrate_balance_channel_fluxes():
     cls[inner & (xs > 1) & (xs < nx - 2)] = FLOW_SOLID | ADE_SOLID
     cls[(cls == 0) & (rng.random(N) < 0.3)] = SINK
     u_in, c_in = 0.03, 0.8
-    o = oracle.Oracle((nx, ny), cls, u_in=u_in, c_in=c_in, k_sink=0.02, tau_c=0.7)
+    o = oracle.Oracle((nx, ny), cls, u_in=u_in, c_in=c_in, k_sink=0.02, tau_c=0.7, k_half=k_half)
     uu = 0.02 * rng.standard_normal((2, N))
     o.step_ade(25, u=uu)
     geq_in = oracle.ade_equilibrium(5, c_in, [u_in, 0.0])
