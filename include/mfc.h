@@ -94,9 +94,15 @@ typedef struct {
     double rho_out;    /* outlet density (pressure reference, normally 1) */
     double c_in;       /* inlet substrate concentration */
     double c_out;      /* outlet concentration for a Dirichlet outlet */
-    double k_sink;     /* first-order consumption rate on sink nodes, in [0, 1) */
+    double k_sink;     /* consumption rate on sink nodes per unit concentration, in [0, 1): the
+                          first-order rate k_sink*C, or the low-concentration slope of the
+                          saturating rate below */
     double u_scale;    /* factor on the flow velocity seen by transport (1 = same units) */
     int ade_outlet;    /* MFC_OUTLET_ZERO_GRADIENT or MFC_OUTLET_DIRICHLET */
+    double k_half;     /* half-saturation concentration K_s of the substrate factor of Eq. 16
+                          (>= 0, lattice concentration units): the consumption on a sink node is
+                          k_sink*C*K_s/(K_s + C), i.e. q_max*C/(C + K_s) with q_max = k_sink*K_s
+                          and the mediator factor folded into k_sink; 0 = first order */
 } mfc_params;
 
 /* Residual of a check at step n: the mean relative change per step since the previous check m,

@@ -70,7 +70,8 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     double *partials;     // NSUM doubles per block (CHECK steps)
     R omega;              // 1 / tau
     R omega_c;            // 1 / tau_c
-    R k_sink;             // consumption rate
+    R k_sink;             // consumption rate per unit concentration (low-concentration slope)
+    R k_half;             // half-saturation concentration K_s of Eq. 16 (0: first order)
     R u_scale;            // factor on the velocity seen by transport
     R rho_out;            // outlet density
     R c_ref;              // offset of the stored transport populations
@@ -581,7 +582,13 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             if (!open) e[i] = R(0);
             cp += e[i];
         }
-        const R sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : R(0);
+        // consumption (Eq. 16's substrate factor): k C, or k C K_s / (K_s + C)
+        R sink = R(0);
+        if (L & (1u << LK::SINK)) {
+            const R Cs = a.c_ref + cp;
+            sink = a.k_sink * Cs;
+            if (a.k_half > R(0)) sink = sink * a.k_half * recip(a.k_half + Cs);
+        }
         R uu_ade = R(0);
         if (A::quadratic) {
 #pragma unroll
@@ -612,7 +619,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 acc[SUM_DC2] = dc * dc;
                 acc[SUM_C2] = Cn * Cn;
                 acc[SUM_C] = Cn;
-                if (L & (1u << LK::SINK)) acc[SUM_CURRENT] = a.k_sink * Cn;
+                acc[SUM_CURRENT] = sink;
                 if (!isfinite(cp)) acc[SUM_BAD] += R(1);
             }
             a.fld_c[k] = open ? cp : -a.c_ref;

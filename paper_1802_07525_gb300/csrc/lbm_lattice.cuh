@@ -159,7 +159,7 @@ enum : int {
     SUM_DC2 = 3,    // sum (C^n - C^(n-1))^2 over transport-open nodes
     SUM_C2 = 4,     // sum C^2
     SUM_C = 5,      // sum C
-    SUM_CURRENT = 6,// sum over consumption nodes of k C
+    SUM_CURRENT = 6,// sum over consumption nodes of the consumption (k C, or k C K_s / (K_s + C))
     SUM_BAD = 7,    // count of non-finite values
     NSUM = 8
 };

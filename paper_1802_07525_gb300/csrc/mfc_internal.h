@@ -32,6 +32,7 @@ struct StepHost {
     double *partials;
     // parameters in double; the argument block holds them in the arithmetic type
     double omega, omega_c, k_sink, u_scale, rho_out, c_ref;
+    double k_half;  // half-saturation concentration of the consumption (0: first order)
     int ade_dirichlet;
     double bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
 };

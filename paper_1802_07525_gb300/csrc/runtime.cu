@@ -130,6 +130,10 @@ mfc_status check_params(const mfc_params *p, std::string *why)
         *why = "inlet/outlet parameters must be finite, densities > 0";
         return MFC_ERR_ARG;
     }
+    if (!fin(p->k_half) || p->k_half < 0.0) {
+        *why = "k_half must be finite and >= 0";
+        return MFC_ERR_ARG;
+    }
     if (p->ade_outlet != MFC_OUTLET_ZERO_GRADIENT && p->ade_outlet != MFC_OUTLET_DIRICHLET) {
         *why = "ade_outlet must be MFC_OUTLET_ZERO_GRADIENT or MFC_OUTLET_DIRICHLET";
         return MFC_ERR_ARG;
@@ -247,6 +251,7 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->omega = 1.0 / p.tau;
     h->omega_c = 1.0 / p.tau_c;
     h->k_sink = p.k_sink;
+    h->k_half = p.k_half;
     h->u_scale = p.u_scale;
     h->rho_out = p.rho_out;
     h->c_ref = L->c_ref;

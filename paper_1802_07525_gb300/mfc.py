@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
                 ("c_in", ctypes.c_double), ("c_out", ctypes.c_double),
                 ("k_sink", ctypes.c_double), ("u_scale", ctypes.c_double),
-                ("ade_outlet", ctypes.c_int)]
+                ("ade_outlet", ctypes.c_int), ("k_half", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -178,8 +178,8 @@ def _ptr(a, ct=ctypes.c_double):
 
 
 def make_params(tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0, c_out=0.0,
-                k_sink=1e-3, u_scale=1.0, ade_outlet=MFC_OUTLET_ZERO_GRADIENT) -> Params:
-    return Params(tau, tau_c, u_in, rho_in, rho_out, c_in, c_out, k_sink, u_scale, ade_outlet)
+                k_sink=1e-3, u_scale=1.0, ade_outlet=MFC_OUTLET_ZERO_GRADIENT, k_half=0.0) -> Params:
+    return Params(tau, tau_c, u_in, rho_in, rho_out, c_in, c_out, k_sink, u_scale, ade_outlet, k_half)
 
 
 def make_desc(shape, bc=None, precision=MFC_FP32, stream=None, ade_q=0) -> LatticeDesc:

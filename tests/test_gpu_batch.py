@@ -184,3 +184,22 @@ def test_batch_boundaries_match_oracle(P, shape, bc):
     assert np.max(np.abs(res["u"] - o.u)) < 1e-5
     assert np.max(np.abs(res["c"] - o.conc)) < 1e-5
     assert np.max(np.abs(res["rho"] - o.rho)) < 1e-5
+
+
+def test_batch_monod_consumption_matches_single_lattice(P):
+    """A request with the saturating consumption (k_half) ends at the same check as the
+    single-lattice solve, with the same current."""
+    w = mi.anode_2d(96, 48, seed=21)
+    kw = dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=0.02, k_half=0.05)
+    b = P.Batch(check_every=100, block=128)
+    t = b.submit(w.shape, w.cls, tol_flow=1e-6, tol_ade=1e-6, max_steps=3000, **kw)
+    b.run()
+    r = b.poll(t)
+    b.close()
+    g = P.Lattice(w.shape, **kw)
+    g.set_geometry(w.cls)
+    s = g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=1e-6, tol_ade=1e-6, max_steps=3000,
+                       check_every=100)
+    g.close()
+    assert r["steps_flow"] == s.steps_flow
+    assert r["current"] == pytest.approx(s.current, rel=1e-5)

@@ -193,3 +193,19 @@ def test_check_step_sums_in_fp64(P):
     assert r.substrate == pytest.approx(s[5], rel=1e-12)
     g.close()
 
+
+
+def test_monod_consumption_fp64(P):
+    """The saturating consumption in the FP64 instantiation: populations and the check-step
+    current within rounding of the oracle."""
+    w = mi.channel_128x64()
+    kw = dict(tau=0.8, tau_c=0.7, u_in=0.01, c_in=1.0, k_sink=0.02, k_half=0.05)
+    g, o = pair(P, w.shape, w.cls, (2, 0), **kw)
+    g.step_coupled(300)
+    o.step_coupled(300)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < TOL64
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < TOL64
+    r = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=2, check_every=2)
+    o.step_coupled(2)
+    assert r.current == pytest.approx(o.sums()[6], rel=1e-12)
+    g.close()

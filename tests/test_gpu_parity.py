@@ -449,3 +449,54 @@ def test_d2q9_transport_launch_shapes_agree_and_fp16_bound(P):
     o.step_coupled(1000)
     _, u, c, _ = g.read_fields()
     assert rel_l2(u, o.u) < 2e-2 and rel_l2(c, o.conc) < 1e-2
+
+
+# ------------------------------------------------------------------------------------------
+# Saturating consumption (Eq. 16's substrate factor, k_half = K_s)
+# ------------------------------------------------------------------------------------------
+
+MONOD = dict(tau=0.8, tau_c=0.7, u_in=0.01, c_in=1.0, k_sink=0.02, k_half=0.05)
+
+
+def test_monod_consumption_channel_populations_and_current(P):
+    """The 128x64 channel with consumption k C K_s / (K_s + C) (K_s = 0.05, about the paper's
+    K_s / C_in = 20 / 410): populations within 1e-5 of the oracle at steps 1, 10, 100, 1000;
+    the check-step current equals the oracle's sum of the same consumption."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **MONOD)
+    done = 0
+    for target in (1, 10, 100, 1000):
+        g.step_coupled(target - done)
+        o.step_coupled(target - done)
+        done = target
+        assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL, target
+        assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL, target
+    r = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=2, check_every=2)
+    o.step_coupled(2)
+    s = o.sums()
+    assert r.current == pytest.approx(s[6], rel=1e-5)
+
+
+def test_monod_consumption_steady_current(P):
+    """Steady solve with the saturating consumption: same stopping check as the oracle, fields
+    and current within 1e-4."""
+    w = mi.channel_128x64()
+    g, o = pair(P, w.shape, w.cls, **MONOD)
+    rg = g.solve_steady(mode=1, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    ro = o.solve_steady(mode=1, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    rho, u, c, cur = g.read_fields()
+    assert rel_l2(c, o.conc) < FIELD_TOL
+    assert abs(rg.current - ro.current) / ro.current < FIELD_TOL
+    assert rg.steps_flow == ro.steps_flow or max(rg.res_flow, ro.res_flow) < 3 * w.tol
+
+
+def test_monod_consumption_3d(P):
+    shape = (19, 13, 11)
+    cls = mi.mark_sink_layer(shape, mi.overlapping_balls(shape, 3, 0.7, 31), mi.SINK)
+    kw = dict(tau=0.7, tau_c=0.6, u_in=0.005, c_in=1.0, k_sink=0.05, k_half=0.1)
+    g, o = pair(P, shape, cls, bc=(1, 0, 2), **kw)
+    g.step_coupled(150)
+    o.step_coupled(150)
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL

@@ -87,6 +87,9 @@ def test_create_rejects_bad_arguments_before_any_allocation(libpath):
     assert b"tau" in L.mfc_last_error(None)
     p = mfc.make_params(k_sink=1.5)
     assert L.mfc_create_lattice(ctypes.byref(d), ctypes.byref(p), ctypes.byref(h)) == mfc.MFC_ERR_ARG
+    p = mfc.make_params(k_half=-0.1)
+    assert L.mfc_create_lattice(ctypes.byref(d), ctypes.byref(p), ctypes.byref(h)) == mfc.MFC_ERR_ARG
+    assert b"k_half" in L.mfc_last_error(None)
     d = mfc.make_desc((8, 8), bc=(mfc.MFC_BC_WALL, mfc.MFC_BC_INOUT))
     p = mfc.make_params()
     assert L.mfc_create_lattice(ctypes.byref(d), ctypes.byref(p), ctypes.byref(h)) == mfc.MFC_ERR_ARG
