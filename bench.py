@@ -322,20 +322,24 @@ def step_bytes(dim, prec_bytes, flow_open, ade_open, ade_q=0):
 
 
 def leg_variants(P, peak):
-    """FP16-storage 2-D step and the 3-D electrode in FP32 and FP16: MLUPS over graph blocks
-    and the plain kernel's fraction of the HBM roofline."""
+    """FP16-storage 2-D step, the D2Q9 transport, the saturating consumption of Eq. 16 and the
+    3-D electrode in FP32 and FP16: MLUPS over graph blocks and the plain kernel's fraction of
+    the HBM roofline."""
     import torch
     import mfc_inputs as mi
     out = {}
     # the FP16 2-D case runs on 4096x1024: its 2048x1024 working set (118 MB) would fit the L2
     cases = [("2d_4096x1024_fp16", mi.anode_2d(4096, 1024), P.MFC_FP16_DEV, 10000),
              ("2d_2048x1024_d2q9_transport_fp32", mi.anode_2d(), P.MFC_FP32, 10000),
+             # K_s = 0.05: the paper's K_s / C_in = 20 / 410 with C_in = 1
+             ("2d_2048x1024_monod_consumption_fp32", mi.anode_2d(), P.MFC_FP32, 10000),
              ("3d_256x128x128_fp32", mi.electrode_3d(), P.MFC_FP32, 5000),
              ("3d_256x128x128_fp16", mi.electrode_3d(), P.MFC_FP16_DEV, 5000)]
     for name, w, prec, steps in cases:
         stream = torch.cuda.Stream()
         aq = 9 if "d2q9" in name else 0
-        lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, ade_q=aq, **wkw(w))
+        kw = dict(wkw(w), k_half=0.05) if "monod" in name else wkw(w)
+        lat = P.Lattice(w.shape, precision=prec, stream=stream.cuda_stream, ade_q=aq, **kw)
         lat.set_geometry(w.cls)
         fo, ao = lat.active_nodes()
         lat.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=1000,
