@@ -420,7 +420,13 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct ReaderBoundar
 // a copy of the last node of the row, store nothing and add nothing, so that the whole block
 // joins the reduction.  acc receives the node's check-step terms.  BFORM: the boundary form
 // (B_BOUNDARY and B_INTERIOR are for tiles that do / do not touch an open boundary).
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ>
+// The consumption law of a kernel: first order (k C), the saturating substrate factor of
+// Eq. 16 (k C K_s / (K_s + C)), or chosen per instance at run time from k_half (batch kernels,
+// whose instances may differ).  Single-lattice step kernels are instantiated per law, so that
+// the first-order kernels carry no code for the other.
+enum : int { SINK_LINEAR = 0, SINK_MONOD = 1, SINK_RUNTIME = 2 };
+
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ, int SINK = SINK_RUNTIME>
 __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, ArithT<ST> (&acc)[NSUM])
 {
     using R = ArithT<ST>;
@@ -584,10 +590,12 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
         }
         // consumption (Eq. 16's substrate factor): k C, or k C K_s / (K_s + C)
         R sink = R(0);
-        if (L & (1u << LK::SINK)) {
+        if constexpr (SINK == SINK_LINEAR) {
+            sink = (L & (1u << LK::SINK)) ? a.k_sink * (a.c_ref + cp) : R(0);
+        } else if (L & (1u << LK::SINK)) {
             const R Cs = a.c_ref + cp;
             sink = a.k_sink * Cs;
-            if (a.k_half > R(0)) sink = sink * a.k_half * recip(a.k_half + Cs);
+            if (SINK == SINK_MONOD || a.k_half > R(0)) sink = sink * a.k_half * recip(a.k_half + Cs);
         }
         R uu_ade = R(0);
         if (A::quadratic) {
@@ -619,7 +627,11 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 acc[SUM_DC2] = dc * dc;
                 acc[SUM_C2] = Cn * Cn;
                 acc[SUM_C] = Cn;
-                acc[SUM_CURRENT] = sink;
+                if constexpr (SINK == SINK_LINEAR) {
+                    if (L & (1u << LK::SINK)) acc[SUM_CURRENT] = a.k_sink * Cn;
+                } else {
+                    acc[SUM_CURRENT] = sink;
+                }
                 if (!isfinite(cp)) acc[SUM_BAD] += R(1);
             }
             a.fld_c[k] = open ? cp : -a.c_ref;
@@ -629,7 +641,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 
 // One step of one lattice: one thread per node, grid (row / block, ny, nz); one reduction
 // partial per block on check steps.
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>()>
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>(), int SINK = SINK_LINEAR>
 __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
     using R = ArithT<ST>;
@@ -643,11 +655,11 @@ __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks)
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
         if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, z))
-            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(a, x0, blockIdx.y, z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY, AQ, SINK>(a, x0, blockIdx.y, z, acc);
         else
-            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR>(a, x0, blockIdx.y, z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR, AQ, SINK>(a, x0, blockIdx.y, z, acc);
     } else {
-        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER>(a, x0, blockIdx.y, z, acc);
+        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER, AQ, SINK>(a, x0, blockIdx.y, z, acc);
     }
     if (MODE == MODE_CHECK)
         block_partials(acc, a.partials + ((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y *

@@ -24,16 +24,27 @@ constexpr int AQ = default_aq<D>();
 #endif
 using Args = StepArgs<D, ST, AQ>;
 
-template <bool FLOW, bool ADE>
-cudaError_t launch_mode(const Args &a, const StepHost &h, cudaStream_t s)
+template <bool FLOW, bool ADE, int SINK>
+cudaError_t launch_sink(const Args &a, const StepHost &h, cudaStream_t s)
 {
     const dim3 grid((unsigned)h.grid, (unsigned)h.geo.ny, (unsigned)h.geo.nz);
     switch (h.mode) {
-    case MODE_PLAIN: lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ><<<grid, h.block, 0, s>>>(a); break;
-    case MODE_WRITE: lbm_step_kernel<D, ST, FLOW, ADE, MODE_WRITE, AQ><<<grid, h.block, 0, s>>>(a); break;
-    default: lbm_step_kernel<D, ST, FLOW, ADE, MODE_CHECK, AQ><<<grid, h.block, 0, s>>>(a); break;
+    case MODE_PLAIN: lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
+    case MODE_WRITE: lbm_step_kernel<D, ST, FLOW, ADE, MODE_WRITE, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
+    default: lbm_step_kernel<D, ST, FLOW, ADE, MODE_CHECK, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
+}
+
+// Steps with transport take the kernels of the lattice's consumption law; flow-only steps have
+// no consumption.
+template <bool FLOW, bool ADE>
+cudaError_t launch_mode(const Args &a, const StepHost &h, cudaStream_t s)
+{
+    if constexpr (ADE) {
+        if (h.k_half > 0.0) return launch_sink<FLOW, ADE, SINK_MONOD>(a, h, s);
+    }
+    return launch_sink<FLOW, ADE, SINK_LINEAR>(a, h, s);
 }
 
 Args make_args(const StepHost &h)
