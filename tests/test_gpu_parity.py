@@ -500,3 +500,26 @@ def test_monod_consumption_3d(P):
     g.step_coupled(150)
     o.step_coupled(150)
     assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+
+
+def test_monod_consumption_d2q9_transport_and_fp16(P):
+    """The saturating-consumption kernels of the D2Q9 transport (FP32) and of FP16 storage:
+    populations against the oracle within the FP32 bound (D2Q9) and the FP16 bound of the
+    first-order kernels (max-abs 5e-3 over 300 steps)."""
+    shape = (150, 37)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N)
+    r = rng.random(N)
+    cls = np.where(r < 0.12, 3, np.where(r < 0.3, 4, 0)).astype(np.uint8)
+    kw = dict(tau=0.8, tau_c=0.7, u_in=0.02, c_in=1.0, k_sink=0.05, k_half=0.05)
+    g, o = pair(P, shape, cls, bc=(2, 1), ade_q=9, **kw)
+    g.step_coupled(300)
+    o.step_coupled(300)
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL
+    g.close()
+    g, o = pair(P, shape, cls, bc=(2, 1), precision=P.MFC_FP16_DEV, **kw)
+    g.step_coupled(300)
+    o.step_coupled(300)
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < 5e-3
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < 5e-3
+    g.close()
