@@ -307,6 +307,26 @@ def test_anode_2048x1024_one_step_parity_at_full_size(P):
     assert maxabs(u, o.u) < 1e-6 and maxabs(c, o.conc) < 1e-6
 
 
+def test_electrode_256x128x128_one_step_parity_at_full_size(P):
+    """The 256x128x128 porous electrode after 100 fused steps: one more GPU step (the step
+    kernel and launch shape the benchmark times) equals one oracle step taken from the GPU's
+    own state, at every node, and so do the velocity and concentration fields."""
+    w = mi.electrode_3d()
+    g = P.Lattice(w.shape, **channel_kw(w))
+    g.set_geometry(w.cls)
+    g.step_coupled(100)
+    o = oracle.Oracle(w.shape, w.cls, **channel_kw(w))
+    o.f[:] = g.read_populations(P.MFC_POP_FLOW)
+    o.g[:] = g.read_populations(P.MFC_POP_ADE)
+    o.step_coupled(1)
+    g.step_coupled(1)
+    assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < 1e-6
+    assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < 1e-6
+    rho, u, c, _ = g.read_fields()
+    assert maxabs(u, o.u) < 1e-6 and maxabs(c, o.conc) < 1e-6
+    g.close()
+
+
 def test_fp16_deviation_storage_error_is_bounded(P):
     """FP16 deviation storage (FP32 arithmetic): the error against the FP64 oracle after 1000
     fused steps is stated rather than held to the FP32 bound; FP16 keeps about 3 significant
