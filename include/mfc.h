@@ -123,7 +123,8 @@ typedef struct {
 typedef struct {
     long steps_flow, steps_ade; /* steps taken by each solver in this call */
     double res_flow, res_ade;   /* residuals at the last check */
-    double current;             /* sum over consumption nodes of k*C at the last check */
+    double current;             /* sum over consumption nodes of the consumption (k*C, or
+                                   k*C*K_s/(K_s + C)) at the last check */
     double mass;                /* sum of rho over flow-open nodes at the last check */
     double substrate;           /* sum of C over transport-open nodes at the last check */
     int status;                 /* the mfc_status the call returned */
