@@ -221,8 +221,13 @@ MFC_API mfc_status mfc_get_launch(mfc_lattice *lat, mfc_launch *launch);
  * transport-blocked, bit 2 consumption), rho[n], u[dim*n] and u_prev[dim*n] (component-major),
  * c[n] and c_prev[n].  Output: out[10] in device memory, the sums sum |u-u_prev|^2, sum |u|^2,
  * sum rho (flow-open nodes), sum (c-c_prev)^2, sum c^2, sum c (transport-open nodes), sum over
- * consumption nodes of k_sink*c, the count of non-finite values, then the flow and transport
- * residuals.  Queued on `stream` (cudaStream_t; NULL for the legacy default stream).
+ * consumption nodes of k_sink*c (the first-order law only: for a lattice with k_half > 0 this is
+ * not the current mfc_solve_steady reports), the count of non-finite values, then the flow and
+ * transport relative changes ||u - u_prev|| / ||u|| and ||c - c_prev|| / ||c|| between the two
+ * snapshots.  These are not divided by the number of steps between the snapshots: divide them
+ * by it to compare with the per-step residuals of mfc_solve_steady.  Queued on `stream`
+ * (cudaStream_t; NULL for the legacy default stream).  A launch failure of this call returns
+ * MFC_ERR_CUDA; an error pending from the caller's earlier work is neither returned nor cleared.
  *
  * It allocates nothing: its per-block partial sums live in a file-scope device array of 512 KiB
  * (256 nodes per block, 8192 blocks) that every GPU which loads the library holds until the

@@ -21,8 +21,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mfc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 BC_WALL, BC_PERIODIC, BC_INOUT = 0, 1, 2
 FLOW_SOLID, ADE_SOLID, SINK = 1, 2, 4
@@ -60,6 +62,44 @@ def build(force: bool = False) -> str:
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
         return _LIB
+
+
+def build_omp(force: bool = False):
+    """Compile the timing-only OpenMP build ``oracle/_build/liboracle_omp.so`` (the same source
+    and flags plus -fopenmp); returns its path, or None when the compiler has no OpenMP."""
+    with _lock:
+        if not force and os.path.exists(_LIB_OMP) and \
+                os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC):
+            return _LIB_OMP
+        os.makedirs(os.path.dirname(_LIB_OMP), exist_ok=True)
+        tmp = _LIB_OMP + f".{os.getpid()}.tmp"
+        r = subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+        return _LIB_OMP
+
+
+def _declare(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    pp = ctypes.POINTER(Params)
+    L.orc_flow_step.argtypes = [pp, u8p, dp, dp, dp, dp]
+    L.orc_ade_step.argtypes = [pp, u8p, dp, dp, dp, dp]
+    return L
+
+
+def lib_omp():
+    """The OpenMP timing build (None where it cannot be built).  Its steps give the same results
+    as the plain build's; only the CPU-baseline timing uses it."""
+    global _lib_omp
+    if _lib_omp is None:
+        path = build_omp()
+        if path is None:
+            return None
+        _lib_omp = _declare(ctypes.CDLL(path))
+    return _lib_omp
 
 
 def lib():
@@ -138,7 +178,11 @@ class Oracle:
 
     def __init__(self, shape, cls=None, *, bc=None, ade_q=None,
                  ade_outlet=0, tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0, c_out=0.0,
-                 k_sink=1e-3, u_scale=1.0, k_half=0.0):
+                 k_sink=1e-3, u_scale=1.0, k_half=0.0, parallel=False):
+        """parallel: step with the OpenMP timing build (CPU-baseline timing only)."""
+        self._steps = lib_omp() if parallel else None
+        if parallel and self._steps is None:
+            raise RuntimeError("the OpenMP build of the oracle is not available")
         shape = tuple(int(s) for s in shape)
         self.dim = len(shape)
         nx, ny = shape[0], shape[1]
@@ -174,7 +218,7 @@ class Oracle:
         self._g2 = np.zeros_like(self.g)
 
     def step_flow(self, n: int = 1):
-        L = lib()
+        L = self._steps or lib()
         for _ in range(n):
             L.orc_flow_step(ctypes.byref(self.p), _u8(self.cls), _d(self.f), _d(self._f2),
                             _d(self.rho), _d(self.u))
@@ -182,7 +226,7 @@ class Oracle:
 
     def step_ade(self, n: int = 1, u=None):
         """Transport steps with the velocity ``u`` (default: the stored flow velocity)."""
-        L = lib()
+        L = self._steps or lib()
         uu = self.u if u is None else np.ascontiguousarray(np.asarray(u, float).reshape(self.dim, self.N))
         for _ in range(n):
             L.orc_ade_step(ctypes.byref(self.p), _u8(self.cls), _d(self.g), _d(self._g2), _d(uu),

@@ -9,6 +9,10 @@
  * back to it.  It shares no code, header, table or constant with the CUDA path.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, round to nearest).
+ * A second, timing-only build adds -fopenmp: the two node loops of a step then share their
+ * rows among the host cores.  Every node's arithmetic is the same in both builds (each node is
+ * written by one thread, from the previous step's values), so their results are identical; the
+ * plain build is the one the tests check against.
  *
  * Conventions (readings of the paper where it is silent or garbled are listed at each place):
  *   - lattice units dx = dt = 1, rho0 = 1;
@@ -277,6 +281,7 @@ ORC_API void orc_flow_step(const orc_params *p, const uint8_t *cls, const double
         bb_in[i] = 2.0 * v.w[i] * p->rho_in * cu / v.cs2;
     }
 
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -331,6 +336,7 @@ ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double 
     ade_equilibrium(&v, p->c_in, uin, geq_in);
     ade_equilibrium(&v, p->c_out, uin, geq_out);
 
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {

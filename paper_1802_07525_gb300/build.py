@@ -36,9 +36,13 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmfc")
 
 
-def _flags(verbose: bool):
+def _flags(verbose: bool, relative: bool = False):
+    """nvcc flags; with ``relative`` the include directories are named relative to the repository
+    root, so that a digest of the flags is the same in every checkout."""
+    inc = "include" if relative else os.path.join(ROOT, "include")
+    src = os.path.relpath(CSRC, ROOT) if relative else CSRC
     f = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-         "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH
+         "-I", inc, "-I", src] + ARCH
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -60,13 +64,14 @@ KERNEL_TU_FILES = ["lbm_launch.cuh", "mfc_internal.h", "lbm_kernels.cuh", "lbm_l
 
 
 def kernel_digest(tu: str) -> str:
-    """Digest of one step-kernel translation unit: its source, the headers it includes and the
-    flags.  A profile taken on a build with the same digest was taken on the same kernel code."""
+    """Digest of one step-kernel translation unit: the contents of its source and of the headers
+    it includes, and the flags with repository-relative paths (no path of the machine enters it).
+    A profile taken on a build with the same digest was taken on the same kernel code."""
     h = hashlib.sha256()
     for name in [tu] + KERNEL_TU_FILES:
         with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(_flags(False)).encode())
+    h.update(" ".join(_flags(False, relative=True)).encode())
     return h.hexdigest()
 
 

@@ -136,11 +136,20 @@ extern "C" MFC_API mfc_status mfc_field_sums_noalloc(long long n, int dim, const
     double *partials = nullptr;
     mfc_status st = scratch_address(&partials);
     if (st != MFC_OK) return st;
-    const int nblocks = (int)((n + NA_BLOCK - 1) / NA_BLOCK);
+    int nblocks = (int)((n + NA_BLOCK - 1) / NA_BLOCK);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    na_sums_kernel<<<nblocks, NA_BLOCK, 0, s>>>(n, dim, node_class, rho, u, u_prev, c, c_prev, k_sink,
-                                                partials);
-    na_finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, out);
-    if (cudaGetLastError() != cudaSuccess) return MFC_ERR_CUDA;
+    // Each launch reports its own error through its return value, so an error left pending by
+    // earlier work of the caller is neither reported as this call's nor cleared.
+    void *sums_args[] = {&n, &dim, &node_class, &rho, &u, &u_prev, &c, &c_prev, &k_sink, &partials};
+    cudaError_t e = cudaLaunchKernel((const void *)na_sums_kernel, dim3((unsigned)nblocks), dim3(NA_BLOCK),
+                                     sums_args, 0, s);
+    if (e == cudaSuccess) {
+        void *fin_args[] = {&partials, &nblocks, &out};
+        e = cudaLaunchKernel((const void *)na_finalize_kernel, dim3(1), dim3(256), fin_args, 0, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // the launch failure just recorded by this call
+        return MFC_ERR_CUDA;
+    }
     return MFC_OK;
 }

@@ -26,9 +26,11 @@ def _dev(torch, a, dtype):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def test_field_sums_noalloc_matches_solve_check(P):
+@pytest.mark.parametrize("case", ["channel_128x64", "electrode_64x32x32"])
+def test_field_sums_noalloc_matches_solve_check(P, case):
     torch = pytest.importorskip("torch")
-    w = mi.channel_128x64()
+    # the 2-D channel, and a 3-D electrode whose velocity has three component planes
+    w = mi.channel_128x64() if case == "channel_128x64" else mi.electrode_3d(64, 32, 32, seed=11)
     kw = dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
     a = P.Lattice(w.shape, **kw)  # steps one by one and hands its fields to the new entry point
     b = P.Lattice(w.shape, **kw)  # reaches the same steps through mfc_solve_steady's check
@@ -52,7 +54,7 @@ def test_field_sums_noalloc_matches_solve_check(P):
         # keep every device tensor referenced until the call's work is done
         d = {k: _dev(torch, v, torch.float64)
              for k, v in dict(rho=rho, u=u, u_prev=u_prev, c=c, c_prev=c_prev).items()}
-        st = L.mfc_field_sums_noalloc(w.nodes, 2, cls.data_ptr(), d["rho"].data_ptr(),
+        st = L.mfc_field_sums_noalloc(w.nodes, w.dim, cls.data_ptr(), d["rho"].data_ptr(),
                                       d["u"].data_ptr(), d["u_prev"].data_ptr(), d["c"].data_ptr(),
                                       d["c_prev"].data_ptr(), w.k_sink, out.data_ptr(),
                                       stream.cuda_stream)
