@@ -47,7 +47,7 @@ class Result(ctypes.Structure):
         ("steps_flow", ctypes.c_long), ("steps_ade", ctypes.c_long),
         ("res_flow", ctypes.c_double), ("res_ade", ctypes.c_double),
         ("current", ctypes.c_double), ("mass", ctypes.c_double), ("substrate", ctypes.c_double),
-        ("converged", ctypes.c_int),
+        ("converged", ctypes.c_int), ("unstable", ctypes.c_int),
     ]
 
 
@@ -239,7 +239,7 @@ class Oracle:
             self.step_ade(1)
 
     def sums(self, u_prev=None, c_prev=None):
-        out = np.zeros(8)
+        out = np.zeros(9)
         up = self.u if u_prev is None else np.ascontiguousarray(u_prev)
         cp = self.conc if c_prev is None else np.ascontiguousarray(c_prev)
         lib().orc_sums(ctypes.byref(self.p), _u8(self.cls), _d(self.rho), _d(self.u), _d(up),

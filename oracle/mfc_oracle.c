@@ -375,23 +375,29 @@ ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double 
  * out[3] = sum (C - C_prev)^2, out[4] = sum C^2,  out[5] = sum C        (transport-active)
  * out[6] = sum over sink nodes of the consumption (the substrate uptake that sets the current,
  *          Eqs. 16, 20)
- * out[7] = number of non-finite values met. */
+ * out[7] = number of non-finite values met
+ * out[8] = number of flow-active nodes outside the range of the scheme: |u|^2 >= cs^2 = 1/3
+ *          (at or above the lattice sound speed, where the low-Mach expansion behind Eq. 5 no
+ *          longer holds) or rho <= 0.  A solver guard: the paper states no such limit. */
 ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho, const double *u,
                       const double *u_prev, const double *conc, const double *conc_prev,
                       double *out)
 {
     long N = n_nodes(p);
-    for (int m = 0; m < 8; ++m) out[m] = 0.0;
+    for (int m = 0; m < 9; ++m) out[m] = 0.0;
     for (long k = 0; k < N; ++k) {
         if (!(cls[k] & CLS_FLOW_SOLID) && rho) {
+            double speed2 = 0.0;
             for (int a = 0; a < p->dim; ++a) {
                 double d = u[a * N + k] - u_prev[a * N + k];
                 out[0] += d * d;
                 out[1] += u[a * N + k] * u[a * N + k];
+                speed2 += u[a * N + k] * u[a * N + k];
                 if (!isfinite(u[a * N + k])) out[7] += 1.0;
             }
             out[2] += rho[k];
             if (!isfinite(rho[k])) out[7] += 1.0;
+            if (speed2 >= 1.0 / 3.0 || rho[k] <= 0.0) out[8] += 1.0;
         }
         if (!(cls[k] & CLS_ADE_SOLID) && conc) {
             double d = conc[k] - conc_prev[k];
@@ -428,6 +434,7 @@ typedef struct {
     long steps_flow, steps_ade;
     double res_flow, res_ade, current, mass, substrate;
     int converged;
+    int unstable;  /* stopped at a check that found flow at or above the sound speed or rho <= 0 */
 } orc_result;
 
 /* Iterate to equilibrium (method steps 2 and 3 of Sec. 3; "enough time steps until an
@@ -437,6 +444,8 @@ typedef struct {
  * evaluated at the check steps n: the multiples of check_every and the last step allowed;
  * m is the previous check step, or the step of the fields given on entry (the last step run
  * before the call).  With check_every = 1 it is the per-step change ||v^n - v^(n-1)|| / ||v^n||.
+ * A check that finds a flow node outside the scheme's range (out[8] of orc_sums) ends the solve
+ * there, not converged, with res->unstable set.
  * SEQUENTIAL: the flow runs to equilibrium, then transport runs with that velocity frozen
  * (the paper's order).  CONCURRENT: both advance together, transport using the same step's
  * flow velocity; both residuals must fall below their tolerances.
@@ -452,7 +461,7 @@ ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f,
     double *g2 = calloc((size_t)va.q * N, sizeof(double));
     double *u_prev = calloc((size_t)d * N, sizeof(double));   /* fields at the previous check */
     double *c_prev = calloc((size_t)N, sizeof(double));
-    double s[8];
+    double s[9];
     memset(res, 0, sizeof *res);
     int conv_f = 0, conv_a = 0;
     if (check_every < 1) check_every = 1;
@@ -471,11 +480,12 @@ ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f,
                 res->mass = s[2];
                 memcpy(u_prev, u, sizeof(double) * d * N);
                 m = n;
+                if (s[8] > 0.0) { res->unstable = 1; break; }
                 if (res->res_flow < tol_flow) { conv_f = 1; break; }
             }
         }
         m = 0;
-        for (long n = 1; n <= max_steps; ++n) {
+        for (long n = 1; n <= max_steps && !res->unstable; ++n) {
             orc_ade_step(p, cls, g, g2, u, conc);
             memcpy(g, g2, sizeof(double) * va.q * N);
             res->steps_ade = n;
@@ -507,6 +517,7 @@ ORC_API int orc_solve_steady(const orc_params *p, const uint8_t *cls, double *f,
                 memcpy(u_prev, u, sizeof(double) * d * N);
                 memcpy(c_prev, conc, sizeof(double) * N);
                 m = n;
+                if (s[8] > 0.0) { res->unstable = 1; break; }
                 if (res->res_flow < tol_flow && res->res_ade < tol_ade) {
                     conv_f = conv_a = 1;
                     break;

@@ -444,6 +444,8 @@ mfc_status retire(mfc_batch *B)
         mfc_status st;
         if (r[SUM_BAD] > 0.0 || !isfinite(r[SUM_MASS]) || !isfinite(r[SUM_C]) || isnan(rf) || isnan(ra))
             st = MFC_ERR_NONFINITE;
+        else if (r[SUM_FAST] > 0.0)
+            st = MFC_ERR_UNSTABLE;
         else if (rf < q.opts.tol_flow && ra < q.opts.tol_ade)
             st = MFC_OK;
         else if (sl.steps >= q.opts.max_steps)

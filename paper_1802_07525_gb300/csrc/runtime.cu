@@ -438,6 +438,7 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
         }
         if (r[SUM_BAD] > 0.0 || !isfinite(r[SUM_MASS]) || !isfinite(r[SUM_C]) || isnan(rf) || isnan(ra))
             return MFC_ERR_NONFINITE;
+        if (r[SUM_FAST] > 0.0) return MFC_ERR_UNSTABLE;
         const bool okf = kind == KIND_ADE || rf < tol_flow;
         const bool oka = kind == KIND_FLOW || ra < tol_ade;
         if (okf && oka) {
@@ -974,6 +975,7 @@ MFC_API const char *mfc_status_string(mfc_status s)
     case MFC_ERR_CUDA: return "CUDA error";
     case MFC_NOT_CONVERGED: return "not converged within the step cap";
     case MFC_ERR_NONFINITE: return "non-finite residual, mass or current";
+    case MFC_ERR_UNSTABLE: return "flow at or above the lattice sound speed, or non-positive density";
     case MFC_ERR_TIMEOUT: return "wall-clock limit reached";
     case MFC_ERR_STATE: return "invalid state";
     case MFC_PENDING: return "pending";

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmfc.so")
 
 MFC_OK, MFC_ERR_ARG, MFC_ERR_OOM, MFC_ERR_OOM_BUDGET, MFC_ERR_CUDA = 0, 1, 2, 3, 4
 MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_TIMEOUT, MFC_ERR_STATE, MFC_PENDING = 5, 6, 7, 8, 9
+MFC_ERR_UNSTABLE = 10
 MFC_BC_WALL, MFC_BC_PERIODIC, MFC_BC_INOUT = 0, 1, 2
 MFC_FP32, MFC_FP16_DEV, MFC_FP64 = 0, 1, 2
 MFC_SEQUENTIAL, MFC_CONCURRENT = 0, 1

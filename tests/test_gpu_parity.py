@@ -543,3 +543,138 @@ def test_monod_consumption_d2q9_transport_and_fp16(P):
     assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < 5e-3
     assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < 5e-3
     g.close()
+
+
+# ------------------------------------------------------------------------------------------
+# 3-D electrode: populations over 1000 steps, steady fields and current
+# ------------------------------------------------------------------------------------------
+
+def electrode_kw(w):
+    return dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
+
+
+def test_3d_electrode_populations_first_1000_steps(P):
+    """Fused D3Q19 + D3Q7 on a 24x20x32 porous electrode (spheres of radius 4, flow along z):
+    populations within 1e-5 of the oracle at steps 1, 10, 100 and 1000."""
+    w = mi.electrode_3d(24, 20, 32, seed=9)
+    g, o = pair(P, w.shape, w.cls, **electrode_kw(w))
+    done = 0
+    for target in (1, 10, 100, 1000):
+        g.step_coupled(target - done)
+        o.step_coupled(target - done)
+        done = target
+        assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL, target
+        assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL, target
+    _, u, c, _ = g.read_fields()
+    assert maxabs(u, o.u) < POP_TOL
+    assert maxabs(c, o.conc) < POP_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_3d_electrode_steady_fields_and_current(P, mode):
+    """The 16x16x24 electrode solved to 1e-7 (checks every 100 steps) in both modes on both
+    sides: velocity and concentration within 1e-4 relative L2, current within 1e-4 relative,
+    the same stopping checks."""
+    w = mi.electrode_3d(16, 16, 24, seed=9)
+    g, o = pair(P, w.shape, w.cls, **electrode_kw(w))
+    rg = g.solve_steady(mode=mode, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    ro = o.solve_steady(mode=mode, tol_flow=w.tol, tol_ade=w.tol, max_steps=w.max_steps,
+                        check_every=100)
+    _, u, c, cur = g.read_fields()
+    assert rg.status == P.MFC_OK and ro.converged
+    assert rel_l2(u, o.u) < FIELD_TOL
+    assert rel_l2(c, o.conc) < FIELD_TOL
+    assert abs(rg.current - ro.current) / ro.current < FIELD_TOL
+    assert abs(cur - ro.current) / ro.current < FIELD_TOL
+    assert abs(rg.steps_flow - ro.steps_flow) <= 100 and abs(rg.steps_ade - ro.steps_ade) <= 100
+    g.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Range guard: a solve whose flow reaches the lattice sound speed stops with its own status
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_flow_at_the_sound_speed_ends_the_solve_at_the_first_check(P, dim):
+    """A uniform flow written through mfc_write_populations into a periodic box is a fixed
+    point of the scheme.  At 0.6 (above the sound speed 0.577) the solve ends at its first check
+    with MFC_ERR_UNSTABLE, as the oracle's does; at 0.55 it runs to its step cap."""
+    shape = (64, 32) if dim == 2 else (32, 16, 16)
+    N = int(np.prod(shape))
+    for speed, expect in ((0.6, P.MFC_ERR_UNSTABLE), (0.55, P.MFC_NOT_CONVERGED)):
+        u = [0.0] * dim
+        u[0] = speed
+        f = np.repeat(oracle.flow_equilibrium(dim, 1.0, u)[:, None], N, axis=1)
+        g = P.Lattice(shape, bc=(1,) * dim, tau=0.8)
+        g.set_geometry(np.zeros(N, np.uint8))
+        g.write_populations(P.MFC_POP_FLOW, f)
+        r = g.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=50, check_every=10)
+        assert r.status == expect
+        assert r.steps_flow == (10 if expect == P.MFC_ERR_UNSTABLE else 50)
+        o = oracle.Oracle(shape, bc=(1,) * dim, tau=0.8)
+        o.f[:] = f
+        ro = o.solve_steady(mode=1, tol_flow=0.0, tol_ade=0.0, max_steps=50, check_every=10)
+        assert ro.unstable == int(expect == P.MFC_ERR_UNSTABLE) and ro.steps_flow == r.steps_flow
+        g.close()
+
+
+# ------------------------------------------------------------------------------------------
+# The paper's units (Table 1): tau = 0.6706, tau_D = 0.5036, and the transport velocity
+# scaled by the ratio of the two lattices' time steps, 17.66
+# ------------------------------------------------------------------------------------------
+
+# Table 1: V = 1.758e-2 mm/s, nu = 1.004 mm^2/s at tau = 0.6706 with dx = 1 mm, so the flow
+# time step is ((tau - 1/2) / 3) / nu = 0.05664 s and the inlet speed in flow lattice units
+# V * dt / dx = 9.957e-4; D = 0.0012 mm^2/s at tau_D = 0.5036 gives a transport time step of 1 s,
+# 17.66 flow steps.
+PAPER_U_IN = 1.758e-2 * ((0.6706 - 0.5) / 3.0) / 1.004
+
+
+def paper_kw(q, u_scale):
+    return dict(tau=0.6706, tau_c=0.5036, u_in=PAPER_U_IN, c_in=1.0, k_sink=1e-3,
+                u_scale=u_scale), (9 if q == 9 else 0)
+
+
+@pytest.mark.parametrize("q", [9, 5])
+@pytest.mark.parametrize("u_scale", [17.66, 1.0])
+def test_paper_units_transport_populations_first_1000_steps(P, q, u_scale):
+    """The 128x64 channel in Table 1's units, with the paper-literal D2Q9 transport (the
+    equilibrium of Eq. 5) and with D2Q5: populations within 1e-5 of the oracle at steps 1, 10,
+    100 and 1000, with transport at the scaled velocity (17.66) and unscaled (1)."""
+    w = mi.channel_128x64()
+    kw, aq = paper_kw(q, u_scale)
+    g = P.Lattice(w.shape, ade_q=aq, **kw)
+    g.set_geometry(w.cls)
+    o = oracle.Oracle(w.shape, w.cls, ade_q=q, **kw)
+    done = 0
+    for target in (1, 10, 100, 1000):
+        g.step_coupled(target - done)
+        o.step_coupled(target - done)
+        done = target
+        assert maxabs(g.read_populations(P.MFC_POP_FLOW), o.f) < POP_TOL, target
+        assert maxabs(g.read_populations(P.MFC_POP_ADE), o.g) < POP_TOL, target
+    g.close()
+
+
+@pytest.mark.parametrize("q", [9, 5])
+def test_paper_units_transport_stability(P, q):
+    """tau_D = 0.5036 is close to the BGK limit 1/2.  With the transport velocity scaled to its
+    own time step (u_scale 17.66, a grid Peclet number of 30 to 75 in the pores) the transport
+    of the 128x64 channel grows without bound after about 2,500 steps, on the GPU as in the
+    oracle; read in the flow's units (u_scale 1) it stays bounded, with the concentration within
+    [-0.01, 1.05] after 20,000 steps."""
+    w = mi.channel_128x64()
+    for u_scale, bounded in ((1.0, True), (17.66, False)):
+        kw, aq = paper_kw(q, u_scale)
+        g = P.Lattice(w.shape, ade_q=aq, **kw)
+        g.set_geometry(w.cls)
+        g.step_coupled(20000 if bounded else 10000)
+        _, _, c, _ = g.read_fields()
+        c = c[(w.cls & 2) == 0]
+        if bounded:
+            assert c.min() > -0.01 and c.max() < 1.05
+        else:
+            assert not (np.isfinite(c).all() and np.abs(c).max() < 10.0)
+        g.close()

@@ -291,14 +291,18 @@ def test_mirror_symmetric_geometry_gives_mirror_symmetric_fields(dim):
 # Transport: diffusion, advection, Dirichlet exponential, sink, balance
 # ------------------------------------------------------------------------------------------
 
-def _gaussian(sig0, dim=2, q=None, tau_c=0.8, u=(0.0, 0.0, 0.0)):
+def _gaussian(sig0, dim=2, q=None, tau_c=0.8, u=(0.0, 0.0, 0.0), u_scale=1.0, v_expect=None):
+    """Error of a Gaussian advected by the frozen field u, which transport sees as u_scale * u,
+    against the closed form moving at v_expect (default u_scale * u); and the relative change
+    of its mass."""
     L = int(16 * sig0)
     shape = (L, L) if dim == 2 else (L, L, L)
     q = q or (5 if dim == 2 else 7)
     cs2 = 0.25 if q == 7 else 1 / 3
     D = cs2 * (tau_c - 0.5)
     t = int(3 * sig0 * sig0 / D / 4)
-    o = oracle.Oracle(shape, bc=(BC_PERIODIC,) * 3, tau_c=tau_c, k_sink=0.0, ade_q=q)
+    o = oracle.Oracle(shape, bc=(BC_PERIODIC,) * 3, tau_c=tau_c, k_sink=0.0, ade_q=q,
+                      u_scale=u_scale)
     k = np.arange(o.N)
     x, y, z = k % L, (k // L) % L, k // (L * L)
     c0 = L // 2
@@ -308,12 +312,13 @@ def _gaussian(sig0, dim=2, q=None, tau_c=0.8, u=(0.0, 0.0, 0.0)):
     for a in range(dim):
         uu[a] = u[a]
     for kk in range(o.N):
-        o.g[:, kk] = oracle.ade_equilibrium(q, C0[kk], list(uu[:, kk]))
+        o.g[:, kk] = oracle.ade_equilibrium(q, C0[kk], list(u_scale * uu[:, kk]))
     o.step_ade(t, u=uu)
     s2 = sig0 ** 2 + 2 * D * t
-    rr = (x - c0 - u[0] * t) ** 2 + (y - c0 - u[1] * t) ** 2
+    v = [u_scale * ua for ua in u] if v_expect is None else list(v_expect)
+    rr = (x - c0 - v[0] * t) ** 2 + (y - c0 - v[1] * t) ** 2
     if dim == 3:
-        rr = rr + (z - c0 - u[2] * t) ** 2
+        rr = rr + (z - c0 - v[2] * t) ** 2
     ex = C0.sum() / (2 * np.pi * s2) ** (dim / 2) * np.exp(-rr / (2 * s2))
     return np.abs(o.conc - ex).max() / ex.max(), o.conc.sum() / C0.sum() - 1.0
 
@@ -334,6 +339,22 @@ def test_gaussian_advection_and_3d_and_d2q9():
     assert e9 < 8e-3
     e3, m3 = _gaussian(3, dim=3)
     assert e3 < 2e-2 and abs(m3) < 1e-13
+
+
+@pytest.mark.parametrize("q", [5, 9])
+def test_velocity_scale_moves_the_gaussian_at_the_scaled_speed(q):
+    """Transport sees the flow velocity times u_scale (the factor between the time steps of
+    the two lattices in the paper's units, Table 1).  A Gaussian in a frozen field u with
+    u_scale = 2.5 moves at 2.5 u: it matches the closed form at the scaled speed as closely as
+    the unscaled Gaussian at that same speed, and is far from the closed form at u itself."""
+    e_scaled, m = _gaussian(4, q=q, u=(0.02, 0.008, 0.0), u_scale=2.5)
+    e_direct, _ = _gaussian(4, q=q, u=(0.05, 0.02, 0.0))
+    assert e_scaled < 8e-3 and abs(m) < 1e-13
+    assert e_scaled == pytest.approx(e_direct, rel=1e-6)
+    # against the closed form at the unscaled speed the same run is far off: over t steps its
+    # centre has moved 1.5 u t further
+    e_unscaled, _ = _gaussian(4, q=q, u=(0.02, 0.008, 0.0), u_scale=2.5, v_expect=(0.02, 0.008, 0.0))
+    assert e_unscaled > 20 * e_scaled
 
 
 def _late_diffusivity(tau_c, q, t1=1000, t2=3000, sig0=4.0, L=64):
@@ -577,6 +598,41 @@ def test_biofilm_rule_cases():
     assert n == 0
 
 
+def test_biofilm_rule_cases_3d():
+    """3-D: the neighbours are the 18 moving directions of the D3Q19 flow set, i.e. the six
+    face and twelve edge neighbours of the 3x3x3 cube around a node, never its eight corners.
+    With prob 1, every open node among them converts; a blocked face neighbour and an open
+    corner neighbour do not."""
+    n = 5
+    N = n ** 3
+
+    def k(x, y, z):
+        return x + n * (y + n * z)
+
+    cls = np.zeros(N, np.uint8)
+    cls[k(2, 2, 2)] = SINK
+    cls[k(3, 2, 2)] = FLOW_SOLID | ADE_SOLID  # a blocked face neighbour
+    o = oracle.Oracle((n, n, n), cls)
+    conc = np.full(N, 0.9)
+    out, cnt = o.biofilm_convert(7, 3, prob=1.0, c_thresh=0.5, conc=conc)
+    faces = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    edges = [(1, 1, 0), (1, -1, 0), (-1, 1, 0), (-1, -1, 0), (1, 0, 1), (1, 0, -1), (-1, 0, 1),
+             (-1, 0, -1), (0, 1, 1), (0, 1, -1), (0, -1, 1), (0, -1, -1)]
+    expect = {k(2 + a, 2 + b, 2 + c) for a, b, c in faces + edges} - {k(3, 2, 2)}
+    assert len(expect) == 17
+    assert set(np.nonzero(out != cls)[0]) == expect and cnt == 17
+    assert all(out[j] == (FLOW_SOLID | SINK) for j in expect)
+    assert out[k(3, 3, 3)] == 0 and out[k(1, 1, 1)] == 0  # corners are not neighbours
+    # the first node scanned is still decided by its own draw: (2,2,1) = node 37, seed 7,
+    # cycle 3: h = splitmix64(7 ^ (3 << 32) ^ 37)
+    h = oracle.splitmix64(7 ^ (3 << 32) ^ k(2, 2, 1))
+    u = (h >> 11) / 2.0 ** 53
+    out, _ = o.biofilm_convert(7, 3, prob=u - 1e-9, c_thresh=0.5, conc=conc)
+    assert out[k(2, 2, 1)] == 0
+    out, _ = o.biofilm_convert(7, 3, prob=u + 1e-9, c_thresh=0.5, conc=conc)
+    assert out[k(2, 2, 1)] == (FLOW_SOLID | SINK)
+
+
 def test_biofilm_rule_rate():
     """On many eligible nodes the converted fraction is prob within binomial bounds."""
     nx, ny = 200, 3
@@ -612,3 +668,46 @@ def test_steady_rest_populations_closed_form():
     sink = (cls & SINK) > 0
     g0 = w0a * o.conc * np.where(sink, 1 - k * tau_c, 1.0)
     assert np.allclose(o.g[0, open_a], g0[open_a], rtol=1e-8, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------
+# Range guard of the solve (no counterpart in the paper: it stops a solve whose flow has left
+# the low-Mach range of the equilibrium of Eq. 5)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_flow_at_the_sound_speed_stops_the_solve_at_the_first_check(dim):
+    """A uniform flow in a periodic box is a fixed point of stream and collide at any speed.
+    Above the sound speed 1/sqrt(3) = 0.577 the solve stops at its first check with the range
+    flag; every open node counts.  Just below it, the same box runs to the step cap."""
+    shape = (12, 6) if dim == 2 else (6, 4, 5)
+    N = int(np.prod(shape))
+    for speed, out in ((0.6, True), (0.55, False)):
+        o = oracle.Oracle(shape, bc=(BC_PERIODIC,) * dim, tau=0.8)
+        u = [0.0] * dim
+        u[0] = speed
+        o.f[:] = oracle.flow_equilibrium(dim, 1.0, u)[:, None]
+        r = o.solve_steady(mode=oracle.CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=50,
+                           check_every=10)
+        assert np.allclose(o.u[0], speed, atol=1e-14, rtol=0)
+        assert r.unstable == int(out) and not r.converged
+        assert r.steps_flow == (10 if out else 50)
+        assert o.sums()[8] == (N if out else 0)
+
+
+def test_range_guard_counts_fast_and_non_positive_density_nodes():
+    """The count of the guard over hand-set fields: nodes with |u|^2 >= 1/3 (on the boundary
+    too) or rho <= 0 among the flow-open nodes; blocked nodes never count."""
+    shape = (8, 4)
+    cls = np.zeros(32, np.uint8)
+    cls[5] = FLOW_SOLID | ADE_SOLID
+    o = oracle.Oracle(shape, cls, bc=(BC_PERIODIC, BC_PERIODIC))
+    o.rho[:] = 1.0
+    o.u[:] = 0.0
+    o.u[0, 1] = 0.6                        # above the sound speed
+    o.u[0, 2], o.u[1, 2] = 0.4, 0.42       # |u|^2 = 0.3364 >= 1/3 by its two components
+    o.u[0, 3] = math.sqrt(1.0 / 3.0) - 1e-9  # just below
+    o.rho[4] = 0.0                         # non-positive density
+    o.u[0, 5] = 0.9                        # blocked: not counted
+    o.rho[6] = 1e-12                       # small but positive
+    assert o.sums()[8] == 3
