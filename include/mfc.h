@@ -184,6 +184,69 @@ MFC_API mfc_status mfc_solve_steady(mfc_lattice *lat, const mfc_solve_opts *opts
 MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *lat, uint64_t seed, uint64_t cycle,
                                     double prob, double c_thresh, long *n_converted);
 
+/* ---- bio-electrochemical model of the anode (host only) -------------------------------- */
+
+/* The electrical side of the model (Sec. 3.2, Eqs. 14-21), lumped over the anode and advanced
+ * once per model iteration (one hour of real time, Sec. 4) from what the steady lattice solve
+ * gives: the mean substrate factor C/(C + K_s) over the biofilm (for a lattice solved with the
+ * saturating consumption, current / (k_sink * k_half * consumption nodes)).  Units: mediator
+ * amounts per unit biomass (mg mediator / mg biomass), q_max per day, currents in A, voltages
+ * in V, resistances in ohm, V_a in L, C^bio in mg biomass / L, time steps in s.  Host arithmetic
+ * in double; no device work, no allocation. */
+typedef struct {
+    double m_total;     /* M_total: total intracellular mediator (Table 1: 0.05) */
+    double mediator_yield; /* Y: mediator yield, mg mediator / mg substrate (0.5687) */
+    double gamma;       /* mediator molar mass, mg / mol (663400) */
+    double m_electrons; /* m: electrons per reduced mediator (2) */
+    double q_max;       /* maximum consumption rate, mg substrate / (mg biomass day) (8.48) */
+    double k_mox;       /* K_Mox: half saturation of the oxidised mediator (0.02 M_total) */
+    double i0;          /* I_0: exchange current density, A / m^2 (0.001) */
+    double e0;          /* E_0: open-circuit voltage, V (0.7) */
+    double r_ext;       /* external (load) resistance, ohm (360) */
+    double r_int;       /* internal resistance, ohm (360) */
+    double epsilon;     /* epsilon of Eq. 20, same units as M_red (not given by the paper) */
+    double area;        /* A_a: anode surface area, m^2 (not given by the paper) */
+    double temperature; /* T, K (not given by the paper) */
+    double volume;      /* V_a: anode compartment volume, L (17 x 60 x 65 mm = 0.0663 L) */
+    double dt;          /* time step of Eq. 15, s */
+    int substeps;       /* Eq. 15 steps per call (each of dt seconds), >= 1 */
+} mfc_electro_params;
+
+typedef struct {
+    double m_ox;      /* M_ox after the call (Eq. 15) */
+    double m_red;     /* M_red = M_total - M_ox after the call (Eq. 14) */
+    double q_a;       /* consumption rate of the last step, mg substrate / (mg biomass day) (Eq. 16) */
+    double n_conc;    /* concentration overpotential of the last step, V (Eq. 18) */
+    double n_act;     /* activation overpotential of the last step, V (Eq. 19) */
+    double i_cell;    /* current of the last step, A (Eq. 20 solved for I, Eqs. 17-19 inside) */
+    double v_cell;    /* I_cell * R_ext, V: the voltage across the load (Eq. 17, and the paper's
+                         reported 330 mV at 0.91 mA) */
+    double v_eq21;    /* I_cell * (R_int + R_ext), V: Eq. 21 as printed */
+} mfc_electro_result;
+
+/* Table 1's values, and for the constants the paper does not give: epsilon = 0.01 (mg mediator /
+ * mg biomass), A_a = 0.0031 m^2 (the electrode's 48 x 65 mm face), T = 298.15 K; V_a = 0.0663 L;
+ * one model iteration (an hour) as 3600 steps of dt = 1 s (an explicit step of an hour would
+ * overshoot the mediator balance, whose relaxation time is about 20 s at these values).
+ * Returns MFC_ERR_ARG for a NULL pointer. */
+MFC_API mfc_status mfc_electro_default_params(mfc_electro_params *p);
+
+/* Advance the mediator balance by p->substeps steps of p->dt seconds, each in the paper's order:
+ *   M_red = M_total - M_ox                                                          (Eq. 14)
+ *   q_a = q_max * S * M_ox / (M_ox + K_Mox), S = substrate_factor                    (Eq. 16)
+ *   n_conc = (R T / F) ln(M_total / M_red)                                          (Eq. 18)
+ *   I = (E_0 - n_conc - n_act) / (R_int + R_ext) * M_red / (epsilon + M_red)        (Eq. 20)
+ *     with n_act = I / (A_a I_0) * R T / (m F) * M_ox / M_red (Eq. 19), which is linear in I,
+ *     so I = (E_0 - n_conc) s / (R_int + R_ext + a s), s = M_red / (epsilon + M_red),
+ *     a = R T / (m F A_a I_0) * M_ox / M_red
+ *   M_ox += dt * (-Y q_a / 86400 + gamma I / (m F V_a C^bio))                         (Eq. 15)
+ * M_ox stays in [0, M_total] (an explicit step that would leave it is cut at the bound).
+ * substrate_factor in [0, 1]; c_bio > 0 (mg biomass / L); m_ox in [0, M_total).  out receives
+ * the state after the call and the last step's rates.  Returns MFC_ERR_ARG for a NULL pointer or
+ * an argument out of range. */
+MFC_API mfc_status mfc_electro_update(const mfc_electro_params *p, double substrate_factor,
+                                      double c_bio, double m_ox, mfc_electro_result *out);
+
 /* ---- reading results and checkpointing (blocking) --------------------------------------- */
 
 /* Fields of the last stepping call, as doubles in host memory (each pointer may be NULL):

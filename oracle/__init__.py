@@ -51,6 +51,35 @@ class Result(ctypes.Structure):
     ]
 
 
+class Electro(ctypes.Structure):
+    """Constants of the bio-electrochemical model (Sec. 3.2, Table 1), in the oracle's units."""
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("M_total", "Y", "gamma", "m", "q_max", "K_Mox", "I_0", "E_0", "R_ext", "R_int",
+                 "eps", "A_a", "T", "V_a", "dt")] + [("substeps", ctypes.c_int)]
+
+
+def electro_table1(**over) -> Electro:
+    """Table 1's values; eps, A_a and T (not in the paper) and the step as given in ``over``,
+    defaulting to eps 0.01, A_a 0.048 x 0.065 m^2, T 298.15 K, V_a 17 x 60 x 65 mm, and one
+    hour as 3600 steps of 1 s."""
+    e = Electro()
+    vals = dict(M_total=0.05, Y=0.5687, gamma=663400.0, m=2.0, q_max=8.48, K_Mox=0.02 * 0.05,
+                I_0=0.001, E_0=0.7, R_ext=360.0, R_int=360.0, eps=0.01, A_a=0.048 * 0.065,
+                T=298.15, V_a=17 * 60 * 65 * 1e-6, dt=1.0, substeps=3600)
+    vals.update(over)
+    for k, v in vals.items():
+        setattr(e, k, v)
+    return e
+
+
+def electro_update(e: Electro, S: float, C_bio: float, M_ox: float) -> dict:
+    """One call of the oracle's bio-electrochemical update (e.substeps steps of Eq. 15)."""
+    out = np.zeros(8)
+    lib().orc_electro_update(ctypes.byref(e), S, C_bio, M_ox, _d(out))
+    return dict(zip(("m_ox", "m_red", "q_a", "n_conc", "n_act", "i_cell", "v_cell", "v_eq21"),
+                    out.tolist()))
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, -ffp-contract=off)."""
     with _lock:
@@ -127,6 +156,10 @@ def lib():
         L.orc_biofilm_convert.argtypes = [pp, u8p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_double, ctypes.c_double, u8p]
         L.orc_biofilm_convert.restype = ctypes.c_long
+        L.orc_electro_update.argtypes = [ctypes.POINTER(Electro), ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, dp]
+        L.orc_electro_size.restype = ctypes.c_int
+        assert L.orc_electro_size() == ctypes.sizeof(Electro)
         L.orc_params_size.restype = ctypes.c_int
         L.orc_result_size.restype = ctypes.c_int
         assert L.orc_params_size() == ctypes.sizeof(Params)

@@ -584,5 +584,72 @@ ORC_API long orc_biofilm_convert(const orc_params *p, const uint8_t *cls, const 
     return count;
 }
 
+/* ------------------------------------------------------------------------------------------
+ * Bio-electrochemical model of the anode, Sec. 3.2, Eqs. 14-21, lumped over the anode.
+ * Units: M_ox, M_red, M_total in mg mediator / mg biomass; q_max in mg substrate /
+ * (mg biomass day); I in A; E_0, overpotentials and voltages in V; resistances in ohm; A_a in
+ * m^2; I_0 in A/m^2; V_a in L; C^bio in mg biomass / L; gamma in mg / mol; dt in s.
+ * Readings (the paper gives the equations but not their time base or every constant):
+ *   - Eq. 15 is an explicit step of dt seconds: the consumption term Y q_a is per day, so it is
+ *     divided by 86400; the current term gamma I / (m F V_a C^bio) is per second;
+ *   - C_s / (C_s + K_s) in Eq. 16 is the mean substrate factor over the biofilm, S, from the
+ *     lattice solve;
+ *   - I in Eq. 20 is implicit (n_act of Eq. 19 depends on I); it is found here as the root of
+ *     g(I) = I - (E_0 - n_conc - n_act(I)) / (R_int + R_ext) * M_red / (eps + M_red)
+ *     by bisection, re-evaluating Eq. 19 at every trial I;
+ *   - the voltage across the load is V = I R_ext (Eq. 17, and the paper's 330 mV at 0.91 mA
+ *     with R_ext = 360 ohm); Eq. 21 as printed, I (R_int + R_ext), is returned beside it;
+ *   - M_ox is kept in [0, M_total (1 - 1e-12)] after each step, so that M_red stays positive.
+ * F = 96485.33212 C/mol and R = 8.314462618 J/(mol K) (exact in the 2019 SI).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    double M_total, Y, gamma, m, q_max, K_Mox, I_0, E_0, R_ext, R_int, eps, A_a, T, V_a, dt;
+    int substeps;
+} orc_electro;
+
+/* out: M_ox, M_red, q_a, n_conc, n_act, I_cell, V (I R_ext), V_eq21 (I (R_int + R_ext)) */
+ORC_API void orc_electro_update(const orc_electro *e, double S, double C_bio, double M_ox,
+                                double *out)
+{
+    const double F = 96485.33212, R = 8.314462618;
+    double q_a = 0.0, n_conc = 0.0, n_act = 0.0, I = 0.0;
+    for (int step = 0; step < e->substeps; ++step) {
+        /* Eq. 14 */
+        double M_red = e->M_total - M_ox;
+        /* Eq. 16 (double Monod) */
+        q_a = e->q_max * S * (M_ox / (M_ox + e->K_Mox));
+        /* Eq. 18 (Nernst) */
+        n_conc = (R * e->T / F) * log(e->M_total / M_red);
+        /* Eq. 20 with Eq. 19 inside: bisection on g(I), which is increasing in I */
+        double lo = -10.0 * fabs(e->E_0) / (e->R_int + e->R_ext) - 1.0;
+        double hi = -lo;
+        for (int it = 0; it < 400; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break; /* no double left between the bounds */
+            double act = mid / (e->A_a * e->I_0) * (R * e->T / (e->m * F)) * (M_ox / M_red);
+            double rhs = (e->E_0 - n_conc - act) / (e->R_int + e->R_ext) * (M_red / (e->eps + M_red));
+            if (mid - rhs > 0.0) hi = mid; else lo = mid;
+        }
+        I = 0.5 * (lo + hi);
+        /* Eq. 19 at the root */
+        n_act = I / (e->A_a * e->I_0) * (R * e->T / (e->m * F)) * (M_ox / M_red);
+        /* Eq. 15 */
+        M_ox = M_ox - e->dt * e->Y * q_a / 86400.0 +
+               e->dt * e->gamma * I / (e->m * F) / (e->V_a * C_bio);
+        if (M_ox < 0.0) M_ox = 0.0;
+        if (M_ox > e->M_total * (1.0 - 1e-12)) M_ox = e->M_total * (1.0 - 1e-12);
+    }
+    out[0] = M_ox;
+    out[1] = e->M_total - M_ox;
+    out[2] = q_a;
+    out[3] = n_conc;
+    out[4] = n_act;
+    out[5] = I;
+    out[6] = I * e->R_ext;
+    out[7] = I * (e->R_int + e->R_ext);
+}
+
+ORC_API int orc_electro_size(void) { return (int)sizeof(orc_electro); }
+
 ORC_API int orc_params_size(void) { return (int)sizeof(orc_params); }
 ORC_API int orc_result_size(void) { return (int)sizeof(orc_result); }

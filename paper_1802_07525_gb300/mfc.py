@@ -89,6 +89,21 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ElectroParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("m_total", "mediator_yield", "gamma", "m_electrons", "q_max", "k_mox", "i0", "e0", "r_ext",
+                 "r_int", "epsilon", "area", "temperature", "volume", "dt")] + \
+               [("substeps", ctypes.c_int)]
+
+
+class ElectroResult(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("m_ox", "m_red", "q_a", "n_conc", "n_act", "i_cell", "v_cell", "v_eq21")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MfcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_string(status)} ({status}): {msg}")
@@ -120,6 +135,10 @@ _SIGS = {
     "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_field_sums_noalloc": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_double, _vp, _vp]),
+    "mfc_electro_default_params": (ctypes.c_int, [ctypes.POINTER(ElectroParams)]),
+    "mfc_electro_update": (ctypes.c_int, [ctypes.POINTER(ElectroParams), ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(ElectroResult)]),
     "mfc_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchOpts), ctypes.POINTER(_vp)]),
     "mfc_batch_destroy": (ctypes.c_int, [_vp]),
     "mfc_batch_submit": (ctypes.c_int, [_vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Params),
@@ -417,6 +436,30 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def electro_params(**over) -> ElectroParams:
+    """The library's defaults (Table 1 and the chosen constants), with fields replaced by
+    ``over`` (``mediator_yield`` is Y)."""
+    p = ElectroParams()
+    st = lib().mfc_electro_default_params(ctypes.byref(p))
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_electro_default_params")
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def electro_update(params: ElectroParams, substrate_factor: float, c_bio: float,
+                   m_ox: float) -> dict:
+    """One call of mfc_electro_update: the mediator balance and the cell's current and voltage
+    after params.substeps steps (Eqs. 14-21)."""
+    r = ElectroResult()
+    st = lib().mfc_electro_update(ctypes.byref(params), substrate_factor, c_bio, m_ox,
+                                  ctypes.byref(r))
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_electro_update")
+    return r.as_dict()
 
 
 def clock() -> float:

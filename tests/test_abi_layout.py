@@ -25,6 +25,8 @@ STRUCTS = {
     "mfc_batch_opts": "BatchOpts",
     "mfc_batch_result": "BatchResult",
     "mfc_batch_stats": "BatchStats",
+    "mfc_electro_params": "ElectroParams",
+    "mfc_electro_result": "ElectroResult",
 }
 
 
