@@ -573,8 +573,8 @@ def leg_batch(P, count, max_steps=0):
         g.close()
     ts = time.perf_counter() - t0
     # field agreement over the solves that ended with finite fields in both arms
-    fin = [(x, y) for x, y in zip(rb, rs)
-           if x["status"] != P.MFC_ERR_NONFINITE and y[0].status != P.MFC_ERR_NONFINITE]
+    bad = (P.MFC_ERR_NONFINITE, P.MFC_ERR_UNSTABLE)
+    fin = [(x, y) for x, y in zip(rb, rs) if x["status"] not in bad and y[0].status not in bad]
     du = max(float(np.linalg.norm(x["u"] - u) / np.linalg.norm(u)) for x, (_, u, _) in fin)
     dc = max(float(np.linalg.norm(x["c"] - c) / np.linalg.norm(c)) for x, (_, _, c) in fin)
     upd = sum(x["steps_flow"] * w.nodes for x, w in zip(rb, works))
@@ -585,6 +585,10 @@ def leg_batch(P, count, max_steps=0):
             "converged": sum(x["status"] == P.MFC_OK for x in rb),
             "at_cap": sum(x["status"] == P.MFC_NOT_CONVERGED for x in rb),
             "nonfinite": sum(x["status"] == P.MFC_ERR_NONFINITE for x in rb),
+            "unstable": [{"instance": i, "shape": list(w.shape), "tau": w.tau, "u_in": w.u_in,
+                          "steps": int(x["steps_flow"]), "alone_steps": int(r.steps_flow)}
+                         for i, (x, w, (r, _, _)) in enumerate(zip(rb, works, rs))
+                         if x["status"] == P.MFC_ERR_UNSTABLE],
             "same_status": sum(x["status"] == r.status for x, (r, _, _) in zip(rb, rs)),
             "same_stop_step": sum(x["steps_flow"] == r.steps_flow for x, (r, _, _) in zip(rb, rs)),
             "max_rel_l2_u_batch_vs_alone": du, "max_rel_l2_c_batch_vs_alone": dc,

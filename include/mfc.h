@@ -184,6 +184,65 @@ MFC_API mfc_status mfc_solve_steady(mfc_lattice *lat, const mfc_solve_opts *opts
 MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *lat, uint64_t seed, uint64_t cycle,
                                     double prob, double c_thresh, long *n_converted);
 
+/* ---- agent-based biofilm (Sec. 3.3) ------------------------------------------------------ */
+
+/* Biofilm formation between steady solves, on a biomass concentration C^bio per node (mg
+ * biomass / L) that the lattice keeps in device memory.  One call runs, in this order:
+ *   attachment: the k_ata front nodes with the smallest keys get C^bio = C_0^bio.  The front is
+ *     the open nodes (class 0) without biomass that have an electrode node (class bits 0 and 1)
+ *     among their flow-lattice neighbours; the key of node k is (top 32 bits of h) << 32 | k,
+ *     h = splitmix64(splitmix64(seed ^ 0x6174746163680000) ^ (cycle << 32) ^ k), so the choice is
+ *     exact and repeatable; every front node when there are fewer than k_ata;
+ *   growth (the double Monod law of Eq. 16): every transport-open node with biomass,
+ *     C^bio <- C^bio (1 + growth * s), s = C+ / (C+ + k_half), C+ = max(C, 0), C the substrate
+ *     concentration of the last stepping call;
+ *   spreading: the nodes above c_max_bio when spreading starts, in increasing node order; one
+ *     still above it when reached passes fr_spr of its biomass to a free neighbour (an open node
+ *     without biomass) drawn at random, or, with none free, to the first cell of a loop-erased
+ *     random walk through the biofilm (steps onto the electrode or out of the lattice are lost)
+ *     that ends on a free cell, after every cell with biomass on the walk's path has passed its
+ *     biomass one cell on towards that free cell; a walk of max_walk steps gives up.  Draw n of
+ *     the pass is splitmix64(splitmix64(seed ^ 0x7370726561640000 ^ (cycle << 32)) ^ n), a choice
+ *     among m options taking (draw >> 32) % m;
+ *   classes: every non-electrode node with biomass becomes biofilm, impermeable to the flow and
+ *     consuming substrate (class 5); the link masks are rebuilt (warm start).
+ * Attachment, growth and the class update are data-parallel kernels; spreading, whose events
+ * move biomass along chains one after another, runs as one device thread.  Growth and the
+ * spreading split are FP64 without contraction; every decision is integer.  Blocks until done. */
+typedef struct {
+    uint64_t seed;
+    int k_ata;          /* front nodes attached per call (Table 1: 200), >= 0 */
+    double c0_bio;      /* C_0^bio, the biomass of an attached node (Table 1: 450), > 0 */
+    double c_max_bio;   /* C_max^bio, the spreading threshold (Table 1: 512.5), > 0 */
+    double fr_spr;      /* fraction of a spreading node's biomass moved (Table 1: 0.4), [0, 1] */
+    double growth;      /* relative growth per call at saturating substrate: the double Monod
+                           rate of Eq. 16 with its mediator factor, times a biomass yield and the
+                           call's time span (not given by the paper), >= 0 */
+    double k_half;      /* K_s of Eq. 16 in lattice concentration units, > 0 */
+    int max_walk;       /* steps a spreading walk may take, 1..65536 */
+} mfc_agent_params;
+
+typedef struct {
+    long long attached;       /* nodes attached by this call */
+    long long front;          /* front nodes it chose among */
+    long long spread;         /* spreading events */
+    long long walks_failed;   /* walks that gave up */
+    long long walk_steps;     /* walk steps taken */
+    long long biofilm_nodes;  /* nodes with biomass after the call */
+    double total_biomass;     /* sum of C^bio after the call (FP64) */
+} mfc_agent_stats;
+
+/* One biofilm-formation step (above).  Fails with MFC_ERR_ARG for a parameter out of range or a
+ * lattice of 2^31 nodes or more.  out is optional.  The biomass starts at zero everywhere. */
+MFC_API mfc_status mfc_agent_step(mfc_lattice *lat, const mfc_agent_params *p, uint64_t cycle,
+                                  mfc_agent_stats *out);
+/* C^bio of every node, N doubles in host memory (zeros before the first step or write). */
+MFC_API mfc_status mfc_read_biomass(mfc_lattice *lat, double *host);
+/* Replace C^bio by N host doubles (each finite and >= 0).  The classes follow at the next
+ * mfc_agent_step; biomass on electrode nodes is never grown or spread and makes no biofilm
+ * (the statistics still count it). */
+MFC_API mfc_status mfc_write_biomass(mfc_lattice *lat, const double *host);
+
 /* ---- bio-electrochemical model of the anode (host only) -------------------------------- */
 
 /* The electrical side of the model (Sec. 3.2, Eqs. 14-21), lumped over the anode and advanced

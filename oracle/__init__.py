@@ -51,6 +51,26 @@ class Result(ctypes.Structure):
     ]
 
 
+class Agent(ctypes.Structure):
+    """Parameters of the agent-based biofilm of Sec. 3.3 (Table 1 gives k_ata, C_0^bio,
+    C_max^bio and fr_spr)."""
+    _fields_ = [("seed", ctypes.c_uint64), ("k_ata", ctypes.c_int), ("C0_bio", ctypes.c_double),
+                ("Cmax_bio", ctypes.c_double), ("fr_spr", ctypes.c_double), ("mu", ctypes.c_double),
+                ("K_s", ctypes.c_double), ("max_walk", ctypes.c_int)]
+
+
+def agent_table1(**over) -> Agent:
+    """Table 1's k_ata = 200, C_0^bio = 450, C_max^bio = 512.5, fr_spr = 0.4; mu = 0.1,
+    K_s = 0.05 and max_walk = 1000 unless given."""
+    a = Agent()
+    vals = dict(seed=0, k_ata=200, C0_bio=450.0, Cmax_bio=512.5, fr_spr=0.4, mu=0.1, K_s=0.05,
+                max_walk=1000)
+    vals.update(over)
+    for k, v in vals.items():
+        setattr(a, k, v)
+    return a
+
+
 class Electro(ctypes.Structure):
     """Constants of the bio-electrochemical model (Sec. 3.2, Table 1), in the oracle's units."""
     _fields_ = [(n, ctypes.c_double) for n in
@@ -156,6 +176,10 @@ def lib():
         L.orc_biofilm_convert.argtypes = [pp, u8p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_double, ctypes.c_double, u8p]
         L.orc_biofilm_convert.restype = ctypes.c_long
+        L.orc_agent_step.argtypes = [pp, u8p, dp, ctypes.POINTER(Agent), ctypes.c_uint64, dp, u8p,
+                                     dp]
+        L.orc_agent_size.restype = ctypes.c_int
+        assert L.orc_agent_size() == ctypes.sizeof(Agent)
         L.orc_electro_update.argtypes = [ctypes.POINTER(Electro), ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, dp]
         L.orc_electro_size.restype = ctypes.c_int
@@ -286,6 +310,20 @@ class Oracle:
                                _d(self.rho), _d(self.u), _d(self.conc), mode, tol_flow, tol_ade,
                                max_steps, check_every, ctypes.byref(r))
         return r
+
+    def agent_step(self, agent: Agent, cycle: int, bio, conc=None):
+        """One agent-based biofilm step (attachment, growth, spreading) on the biomass array
+        ``bio`` (N doubles, updated in place); the classes become the new ones.  ``conc``
+        defaults to the oracle's own concentration field.  Returns the statistics."""
+        c = self.conc if conc is None else np.ascontiguousarray(np.asarray(conc, float).reshape(-1))
+        assert bio.dtype == np.float64 and bio.flags.c_contiguous and bio.size == self.N
+        out = np.zeros_like(self.cls)
+        st = np.zeros(7)
+        lib().orc_agent_step(ctypes.byref(self.p), _u8(self.cls), _d(c), ctypes.byref(agent), cycle,
+                             _d(bio), _u8(out), _d(st))
+        self.cls = out
+        return dict(zip(("attached", "front", "spread", "walks_failed", "walk_steps",
+                         "biofilm_nodes", "total_biomass"), st.tolist()))
 
     def biofilm_convert(self, seed: int, cycle: int, prob: float = 0.05, c_thresh: float = 0.5,
                         conc=None):

@@ -585,6 +585,176 @@ ORC_API long orc_biofilm_convert(const orc_params *p, const uint8_t *cls, const 
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Agent-based biofilm formation, Sec. 3.3: attachment, growth and spreading of biomass, once
+ * per model iteration (between steady solves).  Per node: C^bio (bio[k], mg biomass / L).
+ * Readings where the section leaves a choice:
+ *   - the front is the set of open nodes (no class bit) without biomass that have an electrode
+ *     node (blocked for both lattices) among their flow-lattice neighbours;
+ *   - attachment: the k_ata front nodes with the smallest keys are set to C_0^bio, where the key
+ *     of node k is (the top 32 bits of h) << 32 | k with
+ *     h = splitmix64(splitmix64(seed ^ ATTACH_TAG) ^ (cycle << 32) ^ k); all front nodes when
+ *     there are fewer (keys are unique, so the choice is exact);
+ *   - growth follows the double Monod law of Eq. 16 with the mediator factor, a biomass yield and
+ *     the time span folded into one parameter mu: on every transport-open node with biomass,
+ *     C^bio <- C^bio (1 + mu s), s = C+ / (C+ + K_s), C+ = max(C, 0), C the local substrate
+ *     concentration of the last solve; attachment comes first, so new cells grow too;
+ *   - spreading: the nodes with C^bio > C_max^bio when spreading starts (not electrode) are
+ *     taken in increasing node order; one still above C_max^bio when reached spreads.  Free
+ *     cells are open nodes without biomass inside the lattice.  If a neighbour is free, the
+ *     receiving cell is a random one of its free neighbours (in direction order); otherwise a
+ *     random walk starts at the node: each step draws one of the Q - 1 directions, a step onto
+ *     the electrode or out of the lattice is lost, a step onto a cell already on the walk's path
+ *     erases the loop back to it (loop-erased walk), and the walk ends on the first free cell.
+ *     Every cell with biomass on the path then passes its biomass one cell further along the
+ *     path towards the free cell, which frees the first cell of the path; that cell receives
+ *     fr_spr C^bio of the spreading node, which keeps the rest.  A walk that has taken max_walk
+ *     steps without reaching a free cell gives up (no change);
+ *   - draws of the spreading pass: the n-th draw of the pass is
+ *     splitmix64(splitmix64(seed ^ SPREAD_TAG ^ (cycle << 32)) ^ n), n = 0, 1, ...; a choice
+ *     among m options takes (draw >> 32) % m;
+ *   - afterwards every non-electrode node with biomass is biofilm: impermeable to the flow and
+ *     consuming substrate (class 5; Sec. 3.3 and the conclusions); other classes are kept.
+ * stats: [0] attached, [1] front nodes, [2] spreading events, [3] walks given up,
+ *        [4] walk steps taken, [5] nodes with biomass, [6] total biomass (sum of C^bio).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t seed;
+    int k_ata;
+    double C0_bio, Cmax_bio, fr_spr, mu, K_s;
+    int max_walk;
+} orc_agent;
+
+#define ORC_ATTACH_TAG 0x6174746163680000ULL /* "attach" */
+#define ORC_SPREAD_TAG 0x7370726561640000ULL /* "spread" */
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int inside(const orc_params *p, int x, int y, int z)
+{
+    return x >= 0 && x < p->nx && y >= 0 && y < p->ny && z >= 0 && z < p->nz;
+}
+
+ORC_API void orc_agent_step(const orc_params *p, const uint8_t *cls, const double *conc,
+                            const orc_agent *a, uint64_t cycle, double *bio, uint8_t *cls_out,
+                            double *stats)
+{
+    vset v = flow_set(p);
+    long N = n_nodes(p);
+    const uint8_t ELECTRODE = CLS_FLOW_SOLID | CLS_ADE_SOLID;
+    for (int m = 0; m < 7; ++m) stats[m] = 0.0;
+
+    /* attachment */
+    uint64_t *keys = malloc(sizeof(uint64_t) * (size_t)(N > 0 ? N : 1));
+    long nf = 0;
+    uint64_t base = orc_splitmix64(a->seed ^ ORC_ATTACH_TAG);
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long k = x + (long)p->nx * (y + (long)p->ny * z);
+                if (cls[k] != 0 || bio[k] != 0.0) continue;
+                int front = 0;
+                for (int i = 1; i < v.q; ++i) {
+                    int sx = x + v.c[i][0], sy = y + v.c[i][1], sz = z + v.c[i][2];
+                    if (!inside(p, sx, sy, sz)) continue;
+                    if ((cls[sx + (long)p->nx * (sy + (long)p->ny * sz)] & ELECTRODE) == ELECTRODE) front = 1;
+                }
+                if (!front) continue;
+                uint64_t h = orc_splitmix64(base ^ (cycle << 32) ^ (uint64_t)k);
+                keys[nf++] = ((h >> 32) << 32) | (uint64_t)(uint32_t)k;
+            }
+    qsort(keys, (size_t)nf, sizeof(uint64_t), cmp_u64);
+    long na = nf < a->k_ata ? nf : a->k_ata;
+    for (long j = 0; j < na; ++j) bio[(long)(uint32_t)keys[j]] = a->C0_bio;
+    stats[0] = (double)na;
+    stats[1] = (double)nf;
+    free(keys);
+
+    /* growth (double Monod, Eq. 16) */
+    for (long k = 0; k < N; ++k) {
+        if (bio[k] > 0.0 && !(cls[k] & CLS_ADE_SOLID)) {
+            double C = conc[k] > 0.0 ? conc[k] : 0.0;
+            bio[k] = bio[k] * (1.0 + a->mu * (C / (C + a->K_s)));
+        }
+    }
+
+    /* spreading */
+    long *list = malloc(sizeof(long) * (size_t)(N > 0 ? N : 1));
+    long nl = 0;
+    for (long k = 0; k < N; ++k)
+        if (bio[k] > a->Cmax_bio && !(cls[k] & CLS_ADE_SOLID)) list[nl++] = k;
+    long *path = malloc(sizeof(long) * ((size_t)a->max_walk + 2));
+    uint64_t sbase = orc_splitmix64(a->seed ^ ORC_SPREAD_TAG ^ (cycle << 32));
+    uint64_t ndraw = 0;
+    for (long e = 0; e < nl; ++e) {
+        long k = list[e];
+        if (!(bio[k] > a->Cmax_bio)) continue;
+        int x = (int)(k % p->nx), y = (int)((k / p->nx) % p->ny), z = (int)(k / ((long)p->nx * p->ny));
+        /* free neighbours, in direction order */
+        long freen[19];
+        int nfree = 0;
+        for (int i = 1; i < v.q; ++i) {
+            int sx = x + v.c[i][0], sy = y + v.c[i][1], sz = z + v.c[i][2];
+            if (!inside(p, sx, sy, sz)) continue;
+            long j = sx + (long)p->nx * (sy + (long)p->ny * sz);
+            if (!(cls[j] & ELECTRODE) && bio[j] == 0.0) freen[nfree++] = j;
+        }
+        long target;
+        if (nfree > 0) {
+            uint64_t d = orc_splitmix64(sbase ^ ndraw++);
+            target = freen[(d >> 32) % (uint64_t)nfree];
+        } else {
+            /* loop-erased random walk from k to the first free cell */
+            long len = 1;
+            path[0] = k;
+            int found = 0;
+            for (int step = 0; step < a->max_walk && !found; ++step) {
+                stats[4] += 1.0;
+                uint64_t d = orc_splitmix64(sbase ^ ndraw++);
+                int i = 1 + (int)((d >> 32) % (uint64_t)(v.q - 1));
+                long cur = path[len - 1];
+                int cx = (int)(cur % p->nx), cy = (int)((cur / p->nx) % p->ny);
+                int cz = (int)(cur / ((long)p->nx * p->ny));
+                int sx = cx + v.c[i][0], sy = cy + v.c[i][1], sz = cz + v.c[i][2];
+                if (!inside(p, sx, sy, sz)) continue;
+                long j = sx + (long)p->nx * (sy + (long)p->ny * sz);
+                if (cls[j] & CLS_ADE_SOLID) continue; /* electrode: the step is lost */
+                long at = -1;
+                for (long m = 0; m < len; ++m)
+                    if (path[m] == j) { at = m; break; }
+                if (at >= 0) { len = at + 1; continue; } /* erase the loop */
+                path[len++] = j;
+                if (bio[j] == 0.0) found = 1;
+            }
+            if (!found) { stats[3] += 1.0; continue; }
+            /* shove: every cell with biomass passes it one cell on, from the free end back */
+            for (long m = len - 1; m >= 2; --m) bio[path[m]] = bio[path[m - 1]];
+            target = path[1];
+            bio[target] = 0.0;
+        }
+        double t = a->fr_spr * bio[k];
+        bio[k] = bio[k] - t;
+        bio[target] = t;
+        stats[2] += 1.0;
+    }
+    free(path);
+    free(list);
+
+    /* classes: biomass makes biofilm (impermeable to flow, consuming) */
+    for (long k = 0; k < N; ++k) {
+        cls_out[k] = cls[k];
+        if (bio[k] > 0.0 && !(cls[k] & CLS_ADE_SOLID)) cls_out[k] = CLS_FLOW_SOLID | CLS_SINK;
+        if (bio[k] > 0.0) stats[5] += 1.0;
+        stats[6] += bio[k];
+    }
+}
+
+ORC_API int orc_agent_size(void) { return (int)sizeof(orc_agent); }
+
+/* ------------------------------------------------------------------------------------------
  * Bio-electrochemical model of the anode, Sec. 3.2, Eqs. 14-21, lumped over the anode.
  * Units: M_ox, M_red, M_total in mg mediator / mg biomass; q_max in mg substrate /
  * (mg biomass day); I in A; E_0, overpotentials and voltages in V; resistances in ohm; A_a in

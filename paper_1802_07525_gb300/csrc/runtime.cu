@@ -500,6 +500,12 @@ void release(mfc_lattice *L)
     dev_free(L, L->results_d);
     dev_free(L, L->counts_d);
     dev_free(L, L->staging);
+    dev_free(L, L->biomass);
+    dev_free(L, L->agent_keys);
+    dev_free(L, L->agent_list);
+    dev_free(L, L->agent_mark);
+    dev_free(L, L->agent_path);
+    dev_free(L, L->agent_state);
     if (L->results_h) cudaFreeHost(L->results_h);
     if (L->counts_h) cudaFreeHost(L->counts_h);
     if (L->done) cudaEventDestroy(L->done);
@@ -554,6 +560,15 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
 }
 
 }  // namespace
+
+// Lattice services for the other translation units of the library (the agent-based biofilm).
+mfc_status mfc::lattice_enter(mfc_lattice *L) { return enter(L); }
+mfc_status mfc::lattice_fail(mfc_lattice *L, mfc_status s, const std::string &msg) { return fail(L, s, msg); }
+bool mfc::lattice_alloc(mfc_lattice *L, void **p, size_t bytes) { return dev_alloc(L, p, bytes); }
+mfc_status mfc::lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, int reset)
+{
+    return apply_geometry(L, dev_cls, reset);
+}
 
 mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *params, cudaMemPool_t pool,
                                mfc_lattice **out, std::string *why_out)

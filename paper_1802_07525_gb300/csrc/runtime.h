@@ -50,6 +50,15 @@ struct mfc_lattice {
     float c_ref = 1.0f;
     int grid = 1, block = mfc::DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
 
+    // agent-based biofilm (allocated by the first mfc_agent_step or mfc_write_biomass)
+    double *biomass = nullptr;                // C^bio per node, dense (x fastest)
+    unsigned long long *agent_keys = nullptr; // attachment keys per node
+    int *agent_list = nullptr;                // nodes above C_max^bio, in increasing order
+    int *agent_mark = nullptr;                // position on the current walk's path, or -1
+    int *agent_path = nullptr;                // the walk's path
+    int agent_path_cap = 0;
+    void *agent_state = nullptr;              // selection state and counters
+
     std::vector<mfc::GraphEntry> graphs;
     long flow_open = 0, ade_open = 0;
     double last_current = 0.0;
@@ -70,5 +79,15 @@ mfc_status validate_lattice(const mfc_lattice_desc *desc, const mfc_params *para
 void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h);
 // Seconds on the steady clock (the clock of mfc_clock and of the batch time stamps).
 double now_s();
+// Make the lattice's device current; refuse a lattice with a recorded CUDA error.
+mfc_status lattice_enter(mfc_lattice *L);
+// Record an error on the lattice (CUDA errors stick) and return s.
+mfc_status lattice_fail(mfc_lattice *L, mfc_status s, const std::string &msg);
+// Zero-filled device allocation on the lattice's stream (false when it fails); freed with the
+// lattice.
+bool lattice_alloc(mfc_lattice *L, void **p, size_t bytes);
+// Replace the node classes by the device array dev_cls (N bytes) and rebuild the link masks;
+// reset != 0 returns every open node to rest, else a warm start.  Blocks.
+mfc_status lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, int reset);
 
 }  // namespace mfc

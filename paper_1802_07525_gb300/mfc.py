@@ -89,6 +89,29 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AgentParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("k_ata", ctypes.c_int), ("c0_bio", ctypes.c_double),
+                ("c_max_bio", ctypes.c_double), ("fr_spr", ctypes.c_double),
+                ("growth", ctypes.c_double), ("k_half", ctypes.c_double), ("max_walk", ctypes.c_int)]
+
+
+class AgentStats(ctypes.Structure):
+    _fields_ = [("attached", ctypes.c_longlong), ("front", ctypes.c_longlong),
+                ("spread", ctypes.c_longlong), ("walks_failed", ctypes.c_longlong),
+                ("walk_steps", ctypes.c_longlong), ("biofilm_nodes", ctypes.c_longlong),
+                ("total_biomass", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def agent_params(seed=0, k_ata=200, c0_bio=450.0, c_max_bio=512.5, fr_spr=0.4, growth=0.1,
+                 k_half=0.05, max_walk=1000) -> AgentParams:
+    """Agent-model parameters; the defaults are Table 1's k_ata, C_0^bio, C_max^bio and fr_spr,
+    with a growth of 0.1 per call and K_s = 0.05 (the paper's 20 mg/L against 410 mg/L)."""
+    return AgentParams(seed, k_ata, c0_bio, c_max_bio, fr_spr, growth, k_half, max_walk)
+
+
 class ElectroParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("m_total", "mediator_yield", "gamma", "m_electrons", "q_max", "k_mox", "i0", "e0", "r_ext",
@@ -135,6 +158,10 @@ _SIGS = {
     "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_field_sums_noalloc": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_double, _vp, _vp]),
+    "mfc_agent_step": (ctypes.c_int, [_vp, ctypes.POINTER(AgentParams), ctypes.c_uint64,
+                                      ctypes.POINTER(AgentStats)]),
+    "mfc_read_biomass": (ctypes.c_int, [_vp, _dp]),
+    "mfc_write_biomass": (ctypes.c_int, [_vp, _dp]),
     "mfc_electro_default_params": (ctypes.c_int, [ctypes.POINTER(ElectroParams)]),
     "mfc_electro_update": (ctypes.c_int, [ctypes.POINTER(ElectroParams), ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double,
@@ -293,7 +320,8 @@ class Lattice:
         r = SolveResult()
         # the result is filled for these outcomes; its status field says which one it was
         self._check(self._L.mfc_solve_steady(self.handle, ctypes.byref(o), ctypes.byref(r)),
-                    ok=(MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_TIMEOUT, MFC_ERR_NONFINITE))
+                    ok=(MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_TIMEOUT, MFC_ERR_NONFINITE,
+                        MFC_ERR_UNSTABLE))
         return r
 
     def biofilm_grow(self, seed, cycle, prob=0.05, c_thresh=0.5) -> int:
@@ -301,6 +329,22 @@ class Lattice:
         self._check(self._L.mfc_biofilm_grow(self.handle, seed, cycle, prob, c_thresh,
                                              ctypes.byref(n)))
         return int(n.value)
+
+    def agent_step(self, params: AgentParams, cycle: int) -> dict:
+        """One agent-based biofilm step (attachment, growth, spreading, class update)."""
+        s = AgentStats()
+        self._check(lib().mfc_agent_step(self.handle, ctypes.byref(params), cycle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def read_biomass(self) -> np.ndarray:
+        out = np.empty(self.N, np.float64)
+        self._check(lib().mfc_read_biomass(self.handle, _ptr(out)))
+        return out
+
+    def write_biomass(self, values):
+        v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(-1))
+        assert v.size == self.N
+        self._check(lib().mfc_write_biomass(self.handle, _ptr(v)))
 
     def read_fields(self):
         rho = np.empty(self.N)

@@ -26,6 +26,8 @@ STRUCTS = {
     "mfc_batch_result": "BatchResult",
     "mfc_batch_stats": "BatchStats",
     "mfc_electro_params": "ElectroParams",
+    "mfc_agent_params": "AgentParams",
+    "mfc_agent_stats": "AgentStats",
     "mfc_electro_result": "ElectroResult",
 }
 

@@ -711,3 +711,138 @@ def test_range_guard_counts_fast_and_non_positive_density_nodes():
     o.u[0, 5] = 0.9                        # blocked: not counted
     o.rho[6] = 1e-12                       # small but positive
     assert o.sums()[8] == 3
+
+
+# ------------------------------------------------------------------------------------------
+# Agent-based biofilm (Sec. 3.3): attachment, growth, spreading
+# ------------------------------------------------------------------------------------------
+
+def _electrode_only(shape, seed):
+    import mfc_inputs as mi
+    cls = mi.overlapping_balls(shape, 4 if len(shape) == 3 else 6, 0.7, seed)
+    return np.where((cls & 3) == 3, 3, 0).astype(np.uint8)
+
+
+def _front(o):
+    """The front by brute force over the 3x3(x3) neighbourhood: open nodes without biomass with
+    an electrode node among their neighbours along the flow set's directions."""
+    c, _, _ = oracle.velocity_set(9 if o.dim == 2 else 19)
+    shape = o.shape if o.dim == 3 else (o.shape[0], o.shape[1], 1)
+    cls = o.cls.reshape(shape[::-1])
+    out = set()
+    for z in range(shape[2]):
+        for y in range(shape[1]):
+            for x in range(shape[0]):
+                if cls[z, y, x] != 0:
+                    continue
+                for d in c[1:]:
+                    sx, sy, sz = x + d[0], y + d[1], z + d[2]
+                    if 0 <= sx < shape[0] and 0 <= sy < shape[1] and 0 <= sz < shape[2] \
+                            and cls[sz, sy, sx] == 3:
+                        out.add(x + shape[0] * (y + shape[1] * z))
+                        break
+    return out
+
+
+@pytest.mark.parametrize("shape", [(40, 24), (14, 12, 10)])
+def test_agent_attachment_count_and_choice(shape):
+    """Exactly k_ata front nodes attach, at C_0^bio, and they are the k_ata front nodes with the
+    smallest keys (top 32 bits of the published splitmix64 hash, then the node index); with
+    fewer front nodes than k_ata, all of them attach."""
+    cls = _electrode_only(shape, 5)
+    o = oracle.Oracle(shape, cls)
+    front = _front(o)
+    assert len(front) > 30
+    bio = np.zeros(o.N)
+    a = oracle.agent_table1(seed=11, k_ata=30, mu=0.0, Cmax_bio=1e9)
+    s = o.agent_step(a, 4, bio, conc=np.zeros(o.N))
+    assert s["attached"] == 30 and s["front"] == len(front)
+    got = set(np.nonzero(bio)[0])
+    assert got <= front and np.all(bio[list(got)] == 450.0)
+    base = oracle.splitmix64(11 ^ 0x6174746163680000)
+    keys = sorted(((oracle.splitmix64(base ^ (4 << 32) ^ k) >> 32) << 32 | k) for k in front)
+    assert got == {k & 0xFFFFFFFF for k in keys[:30]}
+    # more than the front: everything attaches; the classes follow the biomass
+    o2 = oracle.Oracle(shape, cls)
+    bio2 = np.zeros(o2.N)
+    s2 = o2.agent_step(oracle.agent_table1(k_ata=10 ** 6, mu=0.0, Cmax_bio=1e9), 0, bio2,
+                       conc=np.zeros(o2.N))
+    assert s2["attached"] == len(front) and set(np.nonzero(bio2)[0]) == front
+    assert np.all(o2.cls[list(front)] == (FLOW_SOLID | SINK))
+
+
+def test_agent_growth_follows_the_monod_closed_form():
+    """Uniform substrate C: after n steps a node's biomass is C_0 (1 + mu C / (C + K_s))^n, and
+    a node at C <= 0 does not grow."""
+    shape = (16, 8)
+    cls = np.zeros(128, np.uint8)
+    cls[:16] = 3                      # an electrode row along y = 0
+    o = oracle.Oracle(shape, cls)
+    bio = np.zeros(128)
+    bio[40] = 100.0
+    bio[41] = 100.0
+    conc = np.full(128, 0.3)
+    conc[41] = -0.01
+    a = oracle.agent_table1(k_ata=0, mu=0.25, K_s=0.1, Cmax_bio=1e12)
+    for n in range(1, 6):
+        o.agent_step(a, n, bio, conc=conc)
+        assert bio[40] == pytest.approx(100.0 * (1 + 0.25 * 0.3 / 0.4) ** n, rel=1e-14)
+        assert bio[41] == 100.0
+
+
+@pytest.mark.parametrize("shape", [(48, 32), (16, 12, 10)])
+def test_agent_spreading_conserves_biomass(shape):
+    """Spreading only moves biomass: over steps with no attachment and no growth the total is
+    kept (to rounding), every spreading node ends with (1 - fr_spr) of what it had, and walks
+    through a dense biofilm happen and end on free cells."""
+    cls = _electrode_only(shape, 9)
+    o = oracle.Oracle(shape, cls)
+    rng = np.random.default_rng(2)
+    bio = np.where(cls == 0, rng.uniform(0, 1000, o.N) * (rng.random(o.N) < 0.6), 0.0)
+    total = bio.sum()
+    a = oracle.agent_table1(seed=5, k_ata=0, mu=0.0, fr_spr=0.4, max_walk=2000)
+    walked = 0
+    for cyc in range(4):
+        before = bio.copy()
+        s = o.agent_step(a, cyc, bio, conc=np.zeros(o.N))
+        walked += s["walk_steps"]
+        assert bio.sum() == pytest.approx(total, rel=1e-13)
+        assert s["total_biomass"] == pytest.approx(total, rel=1e-13)
+        assert np.all(bio >= 0.0)
+        assert np.all(bio[cls == 3] == 0.0)
+        assert s["spread"] > 0
+        # nodes that spread were above the threshold, and a new node holding biomass takes
+        # at most fr_spr of the largest value (its donor's) or a shoved value
+        assert np.count_nonzero(bio) == np.count_nonzero(before) + s["spread"]
+    assert walked > 0
+
+
+def test_agent_spreading_hand_cases():
+    """A lone node above C_max^bio with free neighbours gives fr_spr of its biomass to the one the
+    first draw picks; a node boxed in by biofilm shoves the chain along its walk."""
+    shape = (7, 7)
+    cls = np.zeros(49, np.uint8)
+    o = oracle.Oracle(shape, cls)
+    bio = np.zeros(49)
+    k = 3 + 7 * 3
+    bio[k] = 600.0
+    a = oracle.agent_table1(seed=1, k_ata=0, mu=0.0)
+    s = o.agent_step(a, 2, bio, conc=np.zeros(49))
+    c, _, _ = oracle.velocity_set(9)
+    nbrs = [(3 + d[0]) + 7 * (3 + d[1]) for d in c[1:]]  # all eight are free, in direction order
+    d0 = oracle.splitmix64(oracle.splitmix64(1 ^ 0x7370726561640000 ^ (2 << 32)) ^ 0)
+    j = nbrs[(d0 >> 32) % 8]
+    assert s["spread"] == 1 and s["walk_steps"] == 0
+    assert bio[k] == 600.0 - 0.4 * 600.0 and bio[j] == 0.4 * 600.0
+    assert np.count_nonzero(bio) == 2
+    # boxed in: the 3x3 block around k full of biomass below the threshold
+    o = oracle.Oracle(shape, np.zeros(49, np.uint8))
+    bio = np.zeros(49)
+    for d in c:
+        bio[(3 + d[0]) + 7 * (3 + d[1])] = 100.0
+    bio[k] = 600.0
+    s = o.agent_step(a, 2, bio, conc=np.zeros(49))
+    assert s["spread"] == 1 and s["walk_steps"] >= 2
+    assert bio.sum() == pytest.approx(600.0 + 800.0, rel=1e-15)
+    assert bio[k] == 360.0 and np.count_nonzero(bio) == 10
+    assert sorted(bio[bio > 0].tolist()) == [100.0] * 8 + [240.0, 360.0]
