@@ -486,11 +486,16 @@ def leg_variants(P, peak):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         kern_ms = time_plain_steps(P, lat, stream)
+        # the same kernel with 64-bit element offsets, for comparison
+        lat.set_launch(block=lat.get_launch()["block"], offsets32=0)
+        kern64_ms = time_plain_steps(P, lat, stream)
+        lat.set_launch(block=lat.get_launch()["block"], offsets32=1)
         sb = 2 if prec == P.MFC_FP16_DEV else 4
         byt = step_bytes(w.dim, sb, fo, ao, aq)
         ach = byt / (kern_ms * 1e-3) / 1e9
         out[name] = {"mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
-                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": byt,
+                     "kernel_ms": kern_ms, "kernel_ms_offsets64": kern64_ms,
+                     "algorithmic_bytes_per_launch": byt,
                      "achieved_gbs": ach, "roofline_frac": ach / peak,
                      "bytes_per_node": byt / w.nodes}
         lat.close()

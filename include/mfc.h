@@ -330,6 +330,9 @@ MFC_API mfc_status mfc_synchronize(mfc_lattice *lat);
  * row per block.  Every choice computes the same arithmetic. */
 typedef struct {
     int block;
+    int offsets32;  /* 1 (default): the plain step forms its element offsets in 32 bits where every
+                       population array has fewer than 2^31 elements (one multiply-add per address);
+                       0: 64-bit offsets always */
 } mfc_launch;
 
 /* Select the launch shape (waits for queued work; captured step graphs are rebuilt). */

@@ -426,7 +426,10 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct ReaderBoundar
 // the first-order kernels carry no code for the other.
 enum : int { SINK_LINEAR = 0, SINK_MONOD = 1, SINK_RUNTIME = 2 };
 
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ, int SINK = SINK_RUNTIME>
+// IX: the integer type of the element offsets: long long, or int where every population array
+// has fewer than 2^31 elements (one IMAD.WIDE per address instead of 64-bit offset arithmetic).
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ, int SINK = SINK_RUNTIME,
+          typename IX = long long>
 __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, ArithT<ST> (&acc)[NSUM])
 {
     using R = ArithT<ST>;
@@ -439,7 +442,8 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     const int x = x0 + threadIdx.x;
     if (MODE != MODE_CHECK && x >= g.nx) return;
     const bool valid = MODE != MODE_CHECK || x < g.nx;
-    const long long k = g.at(x < g.nx ? x : g.nx - 1, y, z);
+    const IX k = (IX)g.row0 + (IX)z * (IX)g.zs + (IX)y * (IX)g.px + (IX)(x < g.nx ? x : g.nx - 1);
+    const IX P = (IX)g.plane;
     const uint32_t L = __ldg(a.link + k);
     constexpr bool READER = BFORM != B_WRITER;
     const bool bnd_tile = BFORM == B_WRITER ? tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z)
@@ -475,20 +479,20 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
         R d[F::Q];
 #pragma unroll
         for (int i = 0; i < F::Q; ++i) {
-            const long long off = F::c(i, 0) + (long long)F::c(i, 1) * g.px + (long long)F::c(i, 2) * g.zs;
+            const IX off = (IX)F::c(i, 0) + (IX)F::c(i, 1) * (IX)g.px + (IX)F::c(i, 2) * (IX)g.zs;
             // inlet link (entering across the inlet, no wall in between): moving-wall bounce-back
             const bool bb = i > 0 && ((L >> i) & 1u);
             const bool inj = F::c(i, FA) == 1 && at_in && !bb;
             if (SELECT_LOADS) {
-                const long long o = (bb || inj) ? (long long)F::opp(i) * g.plane : (long long)i * g.plane - off;
-                d[i] = ld(a.fsrc + k + o);
+                const IX o = (bb || inj) ? (IX)F::opp(i) * P : (IX)i * P - off;
+                d[i] = ld(a.fsrc + (k + o));
                 if (F::c(i, FA) == 1 && inj) d[i] += a.bb_in[i];
             } else {
-                const R src = ld(a.fsrc + (long long)i * g.plane + k - off);
+                const R src = ld(a.fsrc + ((IX)i * P + k - off));
                 if (i == 0) {
                     d[0] = src;
                 } else {
-                    const R own = ld(a.fsrc + (long long)F::opp(i) * g.plane + k);
+                    const R own = ld(a.fsrc + ((IX)F::opp(i) * P + k));
                     d[i] = bb ? own : src;
                     if (F::c(i, FA) == 1 && inj) d[i] = own + a.bb_in[i];
                 }
@@ -520,7 +524,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const R feq = weight<F, R>(i) * (rp + (R(1) + rp) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
             const R v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
             moved += v;
-            if (valid) st(a.fdst + (long long)i * g.plane + k, v);
+            if (valid) st(a.fdst + ((IX)i * P + k), v);
         }
         if (valid) st(a.fdst + k, rp - moved);
         if (ghosts && open) {
@@ -561,24 +565,23 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
         R e[A::Q];
 #pragma unroll
         for (int i = 0; i < A::Q; ++i) {
-            const long long off = A::c(i, 0) + (long long)A::c(i, 1) * g.px + (long long)A::c(i, 2) * g.zs;
+            const IX off = (IX)A::c(i, 0) + (IX)A::c(i, 1) * (IX)g.px + (IX)A::c(i, 2) * (IX)g.zs;
             // inlet value; at the outlet, zero gradient (the node's own previous population of the
             // same direction) or the Dirichlet value
             const bool bb = i > 0 && ((L >> (LK::ADE_SELF + i)) & 1u);
             const bool in_v = A::c(i, FA) == 1 && at_in && !bb;
             const bool out_v = A::c(i, FA) == -1 && at_out && !bb;
             if (SELECT_LOADS) {
-                const long long o = bb ? (long long)A::opp(i) * g.plane
-                                       : (long long)i * g.plane - (out_v ? 0 : off);
-                e[i] = ld(a.gsrc + k + o);
+                const IX o = bb ? (IX)A::opp(i) * P : (IX)i * P - (out_v ? (IX)0 : off);
+                e[i] = ld(a.gsrc + (k + o));
             } else {
-                const R src = ld(a.gsrc + (long long)i * g.plane + k - off);
+                const R src = ld(a.gsrc + ((IX)i * P + k - off));
                 if (i == 0) {
                     e[0] = src;
                 } else {
-                    const R own = ld(a.gsrc + (long long)A::opp(i) * g.plane + k);
+                    const R own = ld(a.gsrc + ((IX)A::opp(i) * P + k));
                     e[i] = bb ? own : src;
-                    if (A::c(i, FA) == -1 && out_v) e[i] = ld(a.gsrc + (long long)i * g.plane + k);
+                    if (A::c(i, FA) == -1 && out_v) e[i] = ld(a.gsrc + ((IX)i * P + k));
                 }
             }
             if (A::c(i, FA) == 1 && in_v) e[i] = a.gin_dev[i];
@@ -616,7 +619,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const R geq = weight<A, R>(i) * (cp + (a.c_ref + cp) * shape);
             const R v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - weight<A, R>(i) * sink);
             moved += v;
-            if (valid) st(a.gdst + (long long)i * g.plane + k, v);
+            if (valid) st(a.gdst + ((IX)i * P + k), v);
         }
         if (valid) st(a.gdst + k, cp - sink - moved);
         if (ghosts && open) {
@@ -644,9 +647,11 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 
 // One step of one lattice: one thread per node, grid (row / block, ny, nz); one reduction
 // partial per block on check steps.
-template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>(), int SINK = SINK_LINEAR>
+template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>(), int SINK = SINK_LINEAR,
+          bool IDX32 = false>
 __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
+    using IX = typename std::conditional<IDX32, int, long long>::type;
     using R = ArithT<ST>;
     R acc[NSUM];
 #pragma unroll
@@ -658,11 +663,11 @@ __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks)
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
         if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, blockIdx.y, z))
-            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY, AQ, SINK>(a, x0, blockIdx.y, z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY, AQ, SINK, IX>(a, x0, blockIdx.y, z, acc);
         else
-            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR, AQ, SINK>(a, x0, blockIdx.y, z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR, AQ, SINK, IX>(a, x0, blockIdx.y, z, acc);
     } else {
-        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER, AQ, SINK>(a, x0, blockIdx.y, z, acc);
+        step_node<DIM, ST, FLOW, ADE, MODE, B_WRITER, AQ, SINK, IX>(a, x0, blockIdx.y, z, acc);
     }
     if (MODE == MODE_CHECK)
         block_partials(acc, a.partials + ((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y *

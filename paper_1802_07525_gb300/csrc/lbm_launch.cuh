@@ -29,7 +29,11 @@ cudaError_t launch_sink(const Args &a, const StepHost &h, cudaStream_t s)
 {
     const dim3 grid((unsigned)h.grid, (unsigned)h.geo.ny, (unsigned)h.geo.nz);
     switch (h.mode) {
-    case MODE_PLAIN: lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
+    case MODE_PLAIN:
+        // the plain step, the hot loop: 32-bit element offsets where the arrays allow them
+        if (h.idx32) lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK, true><<<grid, h.block, 0, s>>>(a);
+        else lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK><<<grid, h.block, 0, s>>>(a);
+        break;
     case MODE_WRITE: lbm_step_kernel<D, ST, FLOW, ADE, MODE_WRITE, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
     default: lbm_step_kernel<D, ST, FLOW, ADE, MODE_CHECK, AQ, SINK><<<grid, h.block, 0, s>>>(a); break;
     }

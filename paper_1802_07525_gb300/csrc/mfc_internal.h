@@ -23,6 +23,7 @@ struct StepHost {
     int bc[3];
     int nblocks;      // out: blocks of the launch (one reduction partial each)
     int grid, block;  // grid.x (blocks along a row) and threads per block
+    int idx32;        // every population array has fewer than 2^31 elements: 32-bit offsets
     const void *fsrc;
     void *fdst;
     const void *gsrc;

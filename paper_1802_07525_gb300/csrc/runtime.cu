@@ -237,6 +237,9 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
 
     h->grid = L->grid;
     h->block = L->block;
+    // the largest element offset a step forms is below max(Q_flow, Q_transport) planes
+    const long long qmax = L->qf > L->qa ? L->qf : L->qa;
+    h->idx32 = L->offsets32 && qmax * L->geo.plane < (1ll << 31) ? 1 : 0;
     h->fsrc = L->f[L->fcur];
     h->fdst = L->f[1 - L->fcur];
     h->gsrc = L->g[L->gcur];
@@ -951,8 +954,10 @@ MFC_API mfc_status mfc_set_launch(mfc_lattice *L, const mfc_launch *v)
     if (st != MFC_OK) return st;
     if (!v) return fail(L, MFC_ERR_ARG, "launch is NULL");
     if (v->block != 128 && v->block != 256) return fail(L, MFC_ERR_ARG, "block must be 128 or 256");
+    if (v->offsets32 != 0 && v->offsets32 != 1) return fail(L, MFC_ERR_ARG, "offsets32 must be 0 or 1");
     CK(L, cudaStreamSynchronize(L->stream));
     L->block = v->block;
+    L->offsets32 = v->offsets32;
     choose_launch(L);
     drop_graphs(L);
     return MFC_OK;
@@ -962,6 +967,7 @@ MFC_API mfc_status mfc_get_launch(mfc_lattice *L, mfc_launch *v)
 {
     if (!L || !v) return MFC_ERR_ARG;
     v->block = L->block;
+    v->offsets32 = L->offsets32;
     return MFC_OK;
 }
 

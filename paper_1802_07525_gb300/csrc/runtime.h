@@ -49,6 +49,7 @@ struct mfc_lattice {
     cudaEvent_t done = nullptr;
     float c_ref = 1.0f;
     int grid = 1, block = mfc::DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
+    int offsets32 = 1;  // plain steps with 32-bit element offsets where the arrays allow
 
     // agent-based biofilm (allocated by the first mfc_agent_step or mfc_write_biomass)
     double *biomass = nullptr;                // C^bio per node, dense (x fastest)

@@ -60,7 +60,7 @@ class SolveResult(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int)]
+    _fields_ = [("block", ctypes.c_int), ("offsets32", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -365,8 +365,8 @@ class Lattice:
         v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(q, self.N))
         self._check(self._L.mfc_write_populations(self.handle, which, _ptr(v)))
 
-    def set_launch(self, block=128):
-        v = Launch(int(block))
+    def set_launch(self, block=128, offsets32=1):
+        v = Launch(int(block), int(offsets32))
         self._check(self._L.mfc_set_launch(self.handle, ctypes.byref(v)))
 
     def get_launch(self) -> dict:

@@ -349,7 +349,8 @@ def test_fp16_deviation_storage_error_is_bounded(P):
 # ------------------------------------------------------------------------------------------
 
 def _variants(dim):
-    return [dict(block=128), dict(block=256)]
+    return [dict(block=128), dict(block=256), dict(block=128, offsets32=0),
+            dict(block=256, offsets32=0)]
 
 
 @pytest.mark.parametrize("shape,bc,prec", [
