@@ -66,9 +66,10 @@ typedef enum {
     MFC_ERR_STATE = 8,        /* call not valid in the object's current state */
     MFC_PENDING = 9,          /* a batch request has not finished yet */
     MFC_ERR_UNSTABLE = 10     /* at a check, a flow-open node moved at or above the lattice sound
-                                 speed (|u|^2 >= 1/3) or had rho <= 0: the flow has left the range
-                                 of the low-Mach BGK equilibrium (Eq. 5) and the solve stops there,
-                                 before it turns non-finite */
+                                 speed (|u|^2 >= 1/3) or had a density outside (0, 2): the flow has
+                                 left the weakly compressible, low-Mach range of the BGK
+                                 equilibrium (Eq. 5) and the solve stops there, before it turns
+                                 non-finite */
 } mfc_status;
 
 enum { MFC_BC_WALL = 0, MFC_BC_PERIODIC = 1, MFC_BC_INOUT = 2 };
@@ -167,8 +168,8 @@ MFC_API mfc_status mfc_step_coupled(mfc_lattice *lat, int nsteps);
 /* Iterate to steady state (Sec. 4: "enough time steps until an equilibrium is reached"),
  * checking the residuals every K steps with CUDA-graph replays of K steps.  Blocks.
  * Returns MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_UNSTABLE (first check with a
- * node at or above the sound speed or at rho <= 0) or MFC_ERR_TIMEOUT; out (optional) is
- * filled in every case. */
+ * node at or above the sound speed or with rho outside (0, 2)) or MFC_ERR_TIMEOUT; out
+ * (optional) is filled in every case. */
 MFC_API mfc_status mfc_solve_steady(mfc_lattice *lat, const mfc_solve_opts *opts,
                                     mfc_solve_result *out);
 
@@ -382,9 +383,11 @@ MFC_API mfc_status mfc_field_sums_noalloc(long long n, int dim, const uint8_t *n
  * advance together, every lattice of every instance in one launch per step and dimension (a
  * fixed grid of a few blocks per SM walking a tile table of all instances' rows), in CUDA-graph
  * replays of K steps that end with every instance's residual check.  A finished instance
- * (converged, at its step cap, timed out or non-finite) leaves at the end of its block; its
- * fields are copied to the caller's buffers, its memory goes back to the batch's pool, and
- * waiting requests are admitted before the next block.
+ * (converged, at its step cap, timed out, non-finite or out of range) leaves at the end of its
+ * block; its fields are copied to the caller's buffers while the next block runs, and its memory
+ * goes back to the batch's pool after that block.  Requests that arrive while a block runs are
+ * set up (lattice, classes, link masks) on a second stream during that block and join the next
+ * one, so the host work between blocks overlaps the GPU.
  *
  * What a request gets does not depend on what else runs: every instance steps and checks
  * exactly as it would alone in a batch with the same K and block, bit for bit.  Against
@@ -444,7 +447,9 @@ MFC_API mfc_status mfc_batch_wait(mfc_batch *batch, long long ticket, double tim
 MFC_API mfc_status mfc_batch_run(mfc_batch *batch);
 /* Run the engine on a library thread, which admits requests as they arrive. */
 MFC_API mfc_status mfc_batch_start(mfc_batch *batch);
-/* Stop the engine thread at the end of its current block (requests stay queued or resident). */
+/* Stop the engine thread at the end of its current turn (requests stay queued or resident; a
+ * block it queued may still be in flight, and the next mfc_batch_run or mfc_batch_start takes its
+ * results). */
 MFC_API mfc_status mfc_batch_stop(mfc_batch *batch);
 MFC_API mfc_status mfc_batch_get_stats(mfc_batch *batch, mfc_batch_stats *out);
 /* Text of the batch's last error. */

@@ -255,15 +255,17 @@ class Request:
     porosity: float
 
     def workload(self) -> Workload:
+        # tolerance 1e-7 and the step cap of the batched workload, 3e5, so that FP32 solves
+        # converge instead of stopping at a cap
         if len(self.shape) == 2:
             cls = overlapping_balls(self.shape, 6, self.porosity, self.seed)
             cls = mark_sink_layer(self.shape, cls, SINK)
             return Workload(f"req{self.rid}", self.shape, cls, 0.8, 0.7, 0.01, 1.0, 1e-3, 1e-7,
-                            100000)
+                            300000)
         cls = overlapping_balls(self.shape, 4, self.porosity, self.seed)
         cls = mark_sink_layer(self.shape, cls, SINK)
         return Workload(f"req{self.rid}", self.shape, cls, 0.7, 0.6, 0.005, 1.0, 5e-4, 1e-7,
-                        100000)
+                        300000)
 
 
 def serving_stream(count: int = 2000, rate_per_s: float = 200.0, seed: int = 5,

@@ -378,7 +378,8 @@ ORC_API void orc_ade_step(const orc_params *p, const uint8_t *cls, const double 
  * out[7] = number of non-finite values met
  * out[8] = number of flow-active nodes outside the range of the scheme: |u|^2 >= cs^2 = 1/3
  *          (at or above the lattice sound speed, where the low-Mach expansion behind Eq. 5 no
- *          longer holds) or rho <= 0.  A solver guard: the paper states no such limit. */
+ *          longer holds), or rho <= 0 or rho >= 2 (far from the weakly compressible regime).
+ *          A solver guard: the paper states no such limit. */
 ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho, const double *u,
                       const double *u_prev, const double *conc, const double *conc_prev,
                       double *out)
@@ -397,7 +398,7 @@ ORC_API void orc_sums(const orc_params *p, const uint8_t *cls, const double *rho
             }
             out[2] += rho[k];
             if (!isfinite(rho[k])) out[7] += 1.0;
-            if (speed2 >= 1.0 / 3.0 || rho[k] <= 0.0) out[8] += 1.0;
+            if (speed2 >= 1.0 / 3.0 || rho[k] <= 0.0 || rho[k] >= 2.0) out[8] += 1.0;
         }
         if (!(cls[k] & CLS_ADE_SOLID) && conc) {
             double d = conc[k] - conc_prev[k];
@@ -434,7 +435,7 @@ typedef struct {
     long steps_flow, steps_ade;
     double res_flow, res_ade, current, mass, substrate;
     int converged;
-    int unstable;  /* stopped at a check that found flow at or above the sound speed or rho <= 0 */
+    int unstable;  /* stopped at a check that found a node outside the range (out[8] of orc_sums) */
 } orc_result;
 
 /* Iterate to equilibrium (method steps 2 and 3 of Sec. 3; "enough time steps until an

@@ -1,17 +1,27 @@
 // Batch engine: many steady solves sharing one GPU, with continuous batching (the batch part of
 // the C ABI in include/mfc.h).
 //
-// Requests wait in a first-come-first-served queue; before every block of K steps the engine
-// admits the head of the queue while an instance slot is free and the request's device memory
-// fits the budget.  An admitted request becomes a lattice (mfc_lattice) whose buffers come from
-// the batch's stream-ordered memory pool, so admission and retirement never synchronise the
-// device.  All resident instances of one dimension advance in one launch per step: a fixed grid
-// (resident blocks per SM x SMs) walks a tile table listing every row segment of every
-// instance, instance after instance (lbm_batch_kernel).  A block is a CUDA graph of K steps
-// (K - 1 plain, one check) per group of dimensions present, the per-instance FP64 sums over each
-// instance's tiles, and one copy of all instances' sums to pinned host memory.  After the block
-// the host applies every instance's stopping test; finished instances copy their fields to the
-// caller's buffers and leave, and the tile table is rebuilt for the next block.
+// Requests wait in a first-come-first-served queue and are admitted while an instance slot is
+// free and the request's device memory fits the budget.  An admitted request becomes a lattice
+// (mfc_lattice) whose buffers come from the batch's stream-ordered memory pool.  All active
+// instances of one dimension advance in one launch per step: a fixed grid (resident blocks per
+// SM x SMs) walks a tile table listing every row segment of every instance, instance after
+// instance (lbm_batch_kernel).  A block is a CUDA graph of K steps (K - 1 plain, one check) per
+// group of dimensions present, the per-instance FP64 sums over each instance's tiles, and one
+// copy of all instances' sums to pinned host memory.
+//
+// The host work between blocks overlaps the GPU.  One engine turn, with block b in flight:
+//   1. admit queued requests on a side stream (lattice creation, class upload, link masks);
+//      they wait outside the tables of block b ("joining");
+//   2. wait for block b; free the lattices retired after block b - 1 (their memory is released
+//      in stream order, behind block b);
+//   3. apply every active instance's stopping test to block b's sums; queue the finished ones'
+//      field copies (dense conversion and a copy into pinned staging) on the stream;
+//   4. rebuild the tile tables (finished instances out, joining ones in) and launch block b + 1;
+//   5. while block b + 1 runs: wait for the copies, hand the fields to the callers' buffers and
+//      finish those requests.
+// So the GPU idles between blocks only for the stopping test, the table upload and the graph
+// launch; a request admitted during block b starts with block b + 1.
 //
 // Every instance sees exactly the arithmetic it would see alone: its tiles, partial sums and the
 // order of their addition depend only on its own shape and the batch's block size, and its
@@ -80,10 +90,16 @@ struct Group {
     int grid = 1;
 };
 
+enum { SLOT_FREE = 0, SLOT_ACTIVE = 1, SLOT_JOINING = 2, SLOT_RETIRED = 3 };
+
 struct Slot {
-    std::shared_ptr<Request> req;
+    std::shared_ptr<Request> req;  // the request (kept until the lattice is freed)
     mfc_lattice *L = nullptr;
     long steps = 0;
+    int state = SLOT_FREE;         // ACTIVE: in the tables of the block in flight; JOINING: admitted
+                                   // during a block, active from the next one; RETIRED: finished,
+                                   // its lattice freed once the next block is done
+    size_t stage = 0;              // retiring: offset of its fields in the pinned staging (doubles)
 };
 
 }  // namespace
@@ -98,6 +114,11 @@ struct mfc_batch {
     bool own_stream = false;
     cudaMemPool_t pool = nullptr;
     cudaEvent_t done = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaEvent_t copies = nullptr;   // the finished instances' field copies of this turn
+    cudaStream_t side = nullptr;    // admissions' set-up, overlapping the block in flight
+    bool inflight = false;          // a block is queued and its sums not yet applied
+    double *stage_h = nullptr;      // pinned staging of finished instances' fields
+    size_t stage_cap = 0;           // doubles
     int max_slots = 256;
     int K = 0, block = 0;
     bool tuned = false;
@@ -173,8 +194,11 @@ void drop_graphs(mfc_batch *B)
     }
 }
 
-// Admit queued requests, first come first served, while a slot is free and the head fits.
-mfc_status admit(mfc_batch *B)
+// Admit queued requests, first come first served, while a slot is free and the head fits.  Each
+// lattice is created and set up on stream `s` (the side stream while a block runs, so that the
+// set-up overlaps it), then handed to the batch stream.  With `join`, the new instances wait
+// outside the tables of the block in flight and become active with the next one.
+mfc_status admit(mfc_batch *B, cudaStream_t s, bool join)
 {
     for (;;) {
         std::shared_ptr<Request> r;
@@ -182,9 +206,9 @@ mfc_status admit(mfc_batch *B)
         {
             std::lock_guard<std::mutex> lock(B->mu);
             if (B->queue.empty() || B->sticky != MFC_OK) return B->sticky;
-            for (int s = 0; s < B->max_slots; ++s)
-                if (!B->slots[s].L) {
-                    slot = s;
+            for (int k = 0; k < B->max_slots; ++k)
+                if (B->slots[k].state == SLOT_FREE) {
+                    slot = k;
                     break;
                 }
             if (slot < 0) return MFC_OK;
@@ -197,12 +221,12 @@ mfc_status admit(mfc_batch *B)
             ++B->running;
         }
         mfc_lattice_desc d = r->desc;
-        d.stream = B->stream;
+        d.stream = s;
         mfc_lattice *L = nullptr;
         std::string why;
         mfc_status st = lattice_create(&d, &r->prm, B->pool, &L, &why);
         if (st == MFC_OK) {
-            st = mfc_set_geometry(L, r->cls.data(), 1);
+            st = mfc_set_geometry(L, r->cls.data(), 1);  // waits for stream s only
             if (st != MFC_OK) {
                 why = mfc_last_error(L);
                 mfc_destroy_lattice(L);
@@ -222,10 +246,13 @@ mfc_status admit(mfc_batch *B)
             }
             continue;
         }
+        L->stream = B->stream;  // its set-up on s is complete: from now on it lives on the batch stream
         r->res.t_admit = now_s();
-        B->slots[slot].L = L;
-        B->slots[slot].req = r;
-        B->slots[slot].steps = 0;
+        Slot &sl = B->slots[slot];
+        sl.L = L;
+        sl.req = r;
+        sl.steps = 0;
+        sl.state = join ? SLOT_JOINING : SLOT_ACTIVE;
         B->tables_dirty = true;
     }
 }
@@ -258,7 +285,7 @@ mfc_status rebuild_tables(mfc_batch *B)
         for (int s = 0; s < B->max_slots; ++s) B->grp[gi].ranges_h[s] = make_int2(0, 0);
     for (int s = 0; s < B->max_slots; ++s) {
         mfc_lattice *L = B->slots[s].L;
-        if (!L) continue;
+        if (!L || B->slots[s].state != SLOT_ACTIVE) continue;
         const int gi = L->dim == 2 ? 0 : 1;
         Group &g = B->grp[gi];
         std::vector<Tile> &t = tiles[gi];
@@ -371,7 +398,8 @@ mfc_status autotune(mfc_batch *B)
         // expected steps per solve: the first resident request's cap, at most 20000
         double S = 20000.0;
         for (auto &sl : B->slots)
-            if (sl.L && sl.req->opts.max_steps > 0) S = std::min(S, (double)sl.req->opts.max_steps);
+            if (sl.state == SLOT_ACTIVE && sl.req->opts.max_steps > 0)
+                S = std::min(S, (double)sl.req->opts.max_steps);
         // blocks cost t_o each and a converged solve overshoots by K/2 steps on average:
         // S t_o / K + K t_step / 2 is least at K = sqrt(2 S t_o / t_step)
         double k = sqrt(2.0 * S * t_o / std::max(best, 1e-9));
@@ -422,14 +450,49 @@ mfc_status graph_for(mfc_batch *B, int mask, cudaGraphExec_t *out)
     return MFC_OK;
 }
 
-// Apply every resident instance's stopping test to the sums of the block just run; retire the
-// finished ones.
-mfc_status retire(mfc_batch *B)
+// Pinned staging for `need` doubles of finished instances' fields (its previous contents have
+// been handed out already).
+mfc_status ensure_stage(mfc_batch *B, size_t need)
 {
+    if (need <= B->stage_cap) return MFC_OK;
+    const size_t cap = std::max(need, 2 * B->stage_cap);
+    if (B->stage_h) cudaFreeHost(B->stage_h);
+    B->stage_h = nullptr;
+    B->stage_cap = 0;
+    BCK(B, cudaHostAlloc((void **)&B->stage_h, cap * sizeof(double), cudaHostAllocDefault));
+    B->stage_cap = cap;
+    return MFC_OK;
+}
+
+// Free the lattices retired after the previous block (the stream is idle or runs a block that
+// does not use them: their frees are stream-ordered) and return their memory to the budget.
+void free_retired(mfc_batch *B)
+{
+    for (auto &sl : B->slots) {
+        if (sl.state != SLOT_RETIRED) continue;
+        lattice_destroy_ordered(sl.L);
+        sl.L = nullptr;
+        sl.state = SLOT_FREE;
+        {
+            std::lock_guard<std::mutex> lock(B->mu);
+            B->used -= sl.req->bytes;
+        }
+        sl.req.reset();
+    }
+}
+
+// Apply every active instance's stopping test to the sums of the block just run.  The finished
+// ones leave the tables; the copies of their fields into the pinned staging are queued on the
+// stream (ahead of the next block) and marked by B->copies.  *finished counts them.
+mfc_status retire_decide(mfc_batch *B, int *finished)
+{
+    *finished = 0;
     const double now = now_s();
+    size_t need = 0;
+    std::vector<int> done;
     for (int s = 0; s < B->max_slots; ++s) {
         Slot &sl = B->slots[s];
-        if (!sl.L) continue;
+        if (sl.state != SLOT_ACTIVE) continue;
         sl.steps += B->K;
         const double *r = B->results_h + (size_t)s * NRESULT;
         const double rf = r[RES_FLOW] / B->K, ra = r[RES_ADE] / B->K;
@@ -454,75 +517,158 @@ mfc_status retire(mfc_batch *B)
             st = MFC_ERR_TIMEOUT;
         else
             continue;
+        res.status = st;
         sl.L->last_current = r[SUM_CURRENT];
-        if (q.rho || q.u || q.c) {
-            mfc_status rs = mfc_read_fields(sl.L, q.rho, q.u, q.c, nullptr);
-            if (rs != MFC_OK) st = rs;
-        }
-        mfc_destroy_lattice(sl.L);
-        sl.L = nullptr;
-        std::shared_ptr<Request> req = sl.req;
-        sl.req.reset();
+        sl.state = SLOT_RETIRED;
+        sl.stage = need;
+        if (q.rho || q.u || q.c) need += (size_t)(2 + sl.L->dim) * (size_t)sl.L->N;
+        done.push_back(s);
         B->tables_dirty = true;
-        {
-            std::lock_guard<std::mutex> lock(B->mu);
-            B->used -= req->bytes;
-            --B->running;
-            finish_locked(B, req, st);
-        }
-        if (st == MFC_ERR_CUDA) return batch_fail(B, "reading the fields of a finished instance failed");
+    }
+    *finished = (int)done.size();
+    if (done.empty()) return MFC_OK;
+    mfc_status st = ensure_stage(B, need);
+    if (st != MFC_OK) return st;
+    for (int s : done) {
+        Slot &sl = B->slots[s];
+        Request &q = *sl.req;
+        if (!(q.rho || q.u || q.c)) continue;
+        const size_t N = (size_t)sl.L->N;
+        double *base = B->stage_h + sl.stage;
+        st = lattice_fields_async(sl.L, q.rho ? base : nullptr, q.u ? base + N : nullptr,
+                                  q.c ? base + (1 + sl.L->dim) * N : nullptr);
+        if (st != MFC_OK) return batch_fail(B, "reading the fields of a finished instance failed");
+    }
+    BCK(B, cudaEventRecord(B->copies, B->stream));
+    return MFC_OK;
+}
+
+// Hand the finished instances' fields to their callers (after their copies) and finish the
+// requests.  Their lattices stay allocated until the block now in flight is done.
+mfc_status retire_complete(mfc_batch *B)
+{
+    BCK(B, cudaEventSynchronize(B->copies));
+    for (auto &sl : B->slots) {
+        if (sl.state != SLOT_RETIRED || sl.req->state == REQ_DONE) continue;
+        Request &q = *sl.req;
+        const size_t N = (size_t)sl.L->N;
+        const double *base = B->stage_h + sl.stage;
+        if (q.rho) memcpy(q.rho, base, N * sizeof(double));
+        if (q.u) memcpy(q.u, base + N, (size_t)sl.L->dim * N * sizeof(double));
+        if (q.c) memcpy(q.c, base + (1 + sl.L->dim) * N, N * sizeof(double));
+        std::lock_guard<std::mutex> lock(B->mu);
+        --B->running;
+        finish_locked(B, sl.req, (mfc_status)q.res.result.status);
     }
     return MFC_OK;
 }
 
-// One engine turn: admit, run one block of every resident instance, retire.  *worked = false
-// when nothing was resident.
-mfc_status engine_turn(mfc_batch *B, bool *worked)
+int active_mask(const mfc_batch *B, long long *n_active)
 {
-    *worked = false;
-    mfc_status st = admit(B);
-    if (st != MFC_OK) return st;
     int mask = 0;
+    long long n = 0;
     for (auto &sl : B->slots)
-        if (sl.L) mask |= 1 << (sl.L->dim == 2 ? 0 : 1);
-    if (!mask) return MFC_OK;
-    *worked = true;
+        if (sl.state == SLOT_ACTIVE) {
+            mask |= 1 << (sl.L->dim == 2 ? 0 : 1);
+            ++n;
+        }
+    if (n_active) *n_active = n;
+    return mask;
+}
+
+// Queue one block of every active instance.
+mfc_status launch_block(mfc_batch *B, int mask, long long n_active)
+{
     if (!B->tuned) {
-        st = autotune(B);
+        mfc_status st = autotune(B);
         if (st != MFC_OK) return st;
     }
     if (B->tables_dirty) {
-        st = rebuild_tables(B);
+        mfc_status st = rebuild_tables(B);
         if (st != MFC_OK) return st;
     }
     cudaGraphExec_t exec;
-    st = graph_for(B, mask, &exec);
+    mfc_status st = graph_for(B, mask, &exec);
     if (st != MFC_OK) return st;
     BCK(B, cudaGraphLaunch(exec, B->stream));
     BCK(B, cudaEventRecord(B->done, B->stream));
-    BCK(B, cudaEventSynchronize(B->done));
-    long long n_inst = 0;
-    for (auto &sl : B->slots) n_inst += sl.L != nullptr;
-    {
-        std::lock_guard<std::mutex> lock(B->mu);
-        ++B->blocks;
-        B->instance_steps += n_inst * B->K;
+    B->inflight = true;
+    std::lock_guard<std::mutex> lock(B->mu);
+    ++B->blocks;
+    B->instance_steps += n_active * B->K;
+    return MFC_OK;
+}
+
+// One engine turn (see the file comment).  *worked = false when nothing was in flight, active or
+// joining, and nothing could be admitted.
+mfc_status engine_turn(mfc_batch *B, bool *worked)
+{
+    *worked = false;
+    mfc_status st;
+    if (!B->inflight) {
+        // nothing runs: free what retired, admit straight onto the batch stream, start a block
+        BCK(B, cudaStreamSynchronize(B->stream));
+        free_retired(B);
+        st = admit(B, B->stream, false);
+        if (st != MFC_OK) return st;
+        for (auto &sl : B->slots)
+            if (sl.state == SLOT_JOINING) {
+                sl.state = SLOT_ACTIVE;
+                B->tables_dirty = true;
+            }
+        long long n = 0;
+        const int mask = active_mask(B, &n);
+        if (!mask) return MFC_OK;
+        *worked = true;
+        return launch_block(B, mask, n);
     }
-    return retire(B);
+    *worked = true;
+    // 1. admissions overlap the block in flight
+    st = admit(B, B->side, true);
+    if (st != MFC_OK) return st;
+    // 2. the block's sums
+    BCK(B, cudaEventSynchronize(B->done));
+    B->inflight = false;
+    free_retired(B);
+    // 3. stopping tests; the finished instances' copies go ahead of the next block
+    int finished = 0;
+    st = retire_decide(B, &finished);
+    if (st != MFC_OK) return st;
+    // 4. the next block: joining instances in, finished ones out
+    for (auto &sl : B->slots)
+        if (sl.state == SLOT_JOINING) {
+            sl.state = SLOT_ACTIVE;
+            B->tables_dirty = true;
+        }
+    long long n = 0;
+    const int mask = active_mask(B, &n);
+    if (mask) {
+        st = launch_block(B, mask, n);
+        if (st != MFC_OK) return st;
+    }
+    // 5. results of the finished instances, while the next block runs
+    if (finished) return retire_complete(B);
+    return MFC_OK;
 }
 
 // After a CUDA failure: every unfinished request ends with it.
 void fail_all(mfc_batch *B)
 {
+    cudaStreamSynchronize(B->stream);
+    cudaGetLastError();
+    B->inflight = false;
     for (auto &sl : B->slots) {
         if (!sl.L) continue;
-        mfc_destroy_lattice(sl.L);
+        lattice_destroy_ordered(sl.L);
         sl.L = nullptr;
         std::lock_guard<std::mutex> lock(B->mu);
         B->used -= sl.req->bytes;
-        --B->running;
-        finish_locked(B, sl.req, MFC_ERR_CUDA);
+        if (sl.req->state != REQ_DONE) {
+            --B->running;
+            finish_locked(B, sl.req, MFC_ERR_CUDA);
+        }
         sl.req.reset();
+        sl.state = SLOT_FREE;
     }
     std::lock_guard<std::mutex> lock(B->mu);
     while (!B->queue.empty()) {
@@ -619,6 +765,8 @@ MFC_API mfc_status mfc_batch_create(const mfc_batch_opts *opts, mfc_batch **out)
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->copies, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&B->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&B->t1);
     if (e == cudaSuccess) e = cudaMalloc((void **)&B->results_d, (size_t)B->max_slots * NRESULT * sizeof(double));
@@ -657,6 +805,8 @@ MFC_API mfc_status mfc_batch_destroy(mfc_batch *B)
     if (!B) return MFC_ERR_ARG;
     mfc_batch_stop(B);
     {
+        if (B->stream) cudaStreamSynchronize(B->stream);  // a block may still be in flight
+        if (B->side) cudaStreamSynchronize(B->side);
         for (auto &sl : B->slots)
             if (sl.L) {
                 mfc_destroy_lattice(sl.L);
@@ -668,6 +818,9 @@ MFC_API mfc_status mfc_batch_destroy(mfc_batch *B)
         cudaFree(B->results_d);
         if (B->results_h) cudaFreeHost(B->results_h);
         if (B->done) cudaEventDestroy(B->done);
+        if (B->copies) cudaEventDestroy(B->copies);
+        if (B->side) cudaStreamDestroy(B->side);
+        if (B->stage_h) cudaFreeHost(B->stage_h);
         if (B->t0) cudaEventDestroy(B->t0);
         if (B->t1) cudaEventDestroy(B->t1);
         if (B->pool) cudaMemPoolDestroy(B->pool);

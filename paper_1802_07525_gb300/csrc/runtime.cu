@@ -573,6 +573,45 @@ mfc_status mfc::lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, in
     return apply_geometry(L, dev_cls, reset);
 }
 
+// The fields as dense doubles, queued on the lattice stream into host buffers (each may be null).
+mfc_status mfc::lattice_fields_async(mfc_lattice *L, double *rho, double *u, double *c)
+{
+    mfc_status st = MFC_OK;
+    const size_t N = (size_t)L->N;
+    st = ensure_staging(L, (size_t)(2 + L->dim) * N * sizeof(double));
+    if (st != MFC_OK) return st;
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.geo = L->geo;
+    a.dim = L->dim;
+    a.link = L->link;
+    a.link32 = L->link32;
+    a.flow_self = 0;
+    a.ade_self = L->qf;
+    a.dbl = L->dbl;
+    a.fld_rho = L->fld_rho; a.fld_u = L->fld_u; a.fld_c = L->fld_c;
+    a.c_ref = L->c_ref;
+    a.rho = rho ? L->staging : nullptr;
+    a.u = u ? L->staging + N : nullptr;
+    a.c = c ? L->staging + (1 + L->dim) * N : nullptr;
+    if (rho || u || c) {
+        CK(L, launch_fields_to_dense(a, L->stream));
+        if (rho) CK(L, cudaMemcpyAsync(rho, a.rho, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        if (u) CK(L, cudaMemcpyAsync(u, a.u, L->dim * N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        if (c) CK(L, cudaMemcpyAsync(c, a.c, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    }
+    return MFC_OK;
+}
+
+// Free a lattice whose device buffers come from a stream-ordered pool without waiting for its
+// stream: the frees are queued behind the work already on it.
+void mfc::lattice_destroy_ordered(mfc_lattice *L)
+{
+    if (!L) return;
+    release(L);
+    delete L;
+}
+
 mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *params, cudaMemPool_t pool,
                                mfc_lattice **out, std::string *why_out)
 {
@@ -845,33 +884,14 @@ MFC_API mfc_status mfc_read_fields(mfc_lattice *L, double *rho, double *u, doubl
 {
     mfc_status st = enter(L);
     if (st != MFC_OK) return st;
-    const size_t N = (size_t)L->N;
-    st = ensure_staging(L, (size_t)(2 + L->dim) * N * sizeof(double));
+    st = lattice_fields_async(L, rho, u, c);
     if (st != MFC_OK) return st;
-    ConvArgs a;
-    memset(&a, 0, sizeof a);
-    a.geo = L->geo;
-    a.dim = L->dim;
-    a.link = L->link;
-    a.link32 = L->link32;
-    a.flow_self = 0;
-    a.ade_self = L->qf;
-    a.dbl = L->dbl;
-    a.fld_rho = L->fld_rho; a.fld_u = L->fld_u; a.fld_c = L->fld_c;
-    a.c_ref = L->c_ref;
-    a.rho = rho ? L->staging : nullptr;
-    a.u = u ? L->staging + N : nullptr;
-    a.c = c ? L->staging + (1 + L->dim) * N : nullptr;
-    if (rho || u || c) {
-        CK(L, launch_fields_to_dense(a, L->stream));
-        if (rho) CK(L, cudaMemcpyAsync(rho, a.rho, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-        if (u) CK(L, cudaMemcpyAsync(u, a.u, L->dim * N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-        if (c) CK(L, cudaMemcpyAsync(c, a.c, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-    }
     CK(L, cudaStreamSynchronize(L->stream));
     if (current) *current = L->last_current;
     return MFC_OK;
 }
+
+
 
 static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const double *host_in)
 {
@@ -996,7 +1016,7 @@ MFC_API const char *mfc_status_string(mfc_status s)
     case MFC_ERR_CUDA: return "CUDA error";
     case MFC_NOT_CONVERGED: return "not converged within the step cap";
     case MFC_ERR_NONFINITE: return "non-finite residual, mass or current";
-    case MFC_ERR_UNSTABLE: return "flow at or above the lattice sound speed, or non-positive density";
+    case MFC_ERR_UNSTABLE: return "flow at or above the lattice sound speed, or density outside (0, 2)";
     case MFC_ERR_TIMEOUT: return "wall-clock limit reached";
     case MFC_ERR_STATE: return "invalid state";
     case MFC_PENDING: return "pending";

@@ -90,5 +90,10 @@ bool lattice_alloc(mfc_lattice *L, void **p, size_t bytes);
 // Replace the node classes by the device array dev_cls (N bytes) and rebuild the link masks;
 // reset != 0 returns every open node to rest, else a warm start.  Blocks.
 mfc_status lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, int reset);
+// The fields of the last stepping call as dense doubles (as mfc_read_fields gives them), queued
+// on the lattice stream into host buffers (each may be null); the caller waits for the stream.
+mfc_status lattice_fields_async(mfc_lattice *L, double *rho, double *u, double *c);
+// Free a pooled lattice without waiting for its stream (its frees are stream-ordered).
+void lattice_destroy_ordered(mfc_lattice *L);
 
 }  // namespace mfc

@@ -121,19 +121,43 @@ def test_admission_within_budget_first_come_first_served(P):
 
 
 def test_engine_thread_admits_requests_arriving_while_others_run(P):
-    works = mix()[:4]
+    """Continuous batching: a request submitted while another has already run blocks is set up
+    during a running block and joins between blocks; the first request keeps running (it
+    finishes after the second was admitted, with no restart), and each result is bit-identical
+    to the same request solved alone (same K and block)."""
+    import time
+    first, second = mi.anode_2d(160, 80, seed=41), mi.electrode_3d(20, 16, 24, seed=42)
+    opts = dict(tol_flow=0.0, tol_ade=0.0)  # run to the cap: a known number of blocks
     b = P.Batch(check_every=100, block=128)
     b.start()
-    tickets = []
-    for w in works:
-        tickets.append(b.submit(w.shape, w.cls, tol_flow=1e-6, tol_ade=1e-6, max_steps=2000,
-                                **kw(w)))
-    res = [b.wait(t, timeout_s=120.0) for t in tickets]
+    t1 = b.submit(first.shape, first.cls, max_steps=6000, **opts, **kw(first))
+    deadline = time.monotonic() + 60.0
+    while b.stats()["blocks"] < 3 and time.monotonic() < deadline:
+        time.sleep(0.001)
+    blocks_before = b.stats()["blocks"]
+    assert blocks_before >= 3, "the first request never ran"
+    t2 = b.submit(second.shape, second.cls, max_steps=3000, **opts, **kw(second))
+    r2 = b.wait(t2, timeout_s=120.0)
+    r1 = b.wait(t1, timeout_s=120.0)
+    st = b.stats()
     b.stop()
-    assert all(r is not None for r in res)
-    assert all(r["t_done"] >= r["t_admit"] >= r["t_submit"] for r in res)
-    assert b.stats()["completed"] == len(works)
     b.close()
+    assert r1 is not None and r2 is not None
+    # the second was admitted after the first had run blocks, while the first was running, and
+    # the first went on to its cap without interruption
+    assert r2["t_admit"] > r1["t_admit"] and r2["t_admit"] < r1["t_done"]
+    assert r1["steps_flow"] == 6000 and r2["steps_flow"] == 3000
+    assert r1["status"] == r2["status"] == P.MFC_NOT_CONVERGED
+    # blocks ran both together: fewer blocks than running them one after the other
+    assert st["blocks"] < 60 + 30
+    # bit for bit the results of the same requests alone
+    alone1, _ = solve_in_batch(P, [first], max_steps=6000, tol=0.0)
+    alone2, _ = solve_in_batch(P, [second], max_steps=3000, tol=0.0)
+    for a, m in ((alone1[0], r1), (alone2[0], r2)):
+        for k in ("steps_flow", "res_flow", "res_ade", "current", "mass", "substrate"):
+            assert a[k] == m[k], k
+        for k in ("rho", "u", "c"):
+            assert np.array_equal(a[k], m[k]), k
 
 
 def test_bad_requests_are_refused(P):
