@@ -88,6 +88,11 @@ typedef struct {
                          with the linear equilibrium), or 9 in 2-D: D2Q9 with the equilibrium
                          of Eq. 5, C in place of rho (the text after Eq. 12); batches take the
                          default only */
+    int cut[2];       /* slab decomposition along the flow axis: cut[0] (cut[1]) = 1 makes the
+                         low (high) face of the flow axis a cut to a neighbouring slab, whose
+                         crossing populations arrive through mfc_halo_unpack instead of the
+                         axis' boundary kind (0 for a whole lattice; a lattice with a cut may not
+                         be periodic along the flow axis; batches take no cuts) */
     void *stream;     /* cudaStream_t, or NULL for a library-owned stream */
 } mfc_lattice_desc;
 
@@ -339,6 +344,36 @@ typedef struct {
 /* Select the launch shape (waits for queued work; captured step graphs are rebuilt). */
 MFC_API mfc_status mfc_set_launch(mfc_lattice *lat, const mfc_launch *launch);
 MFC_API mfc_status mfc_get_launch(mfc_lattice *lat, mfc_launch *launch);
+
+/* ---- slab decomposition (one lattice split along the flow axis) ------------------------- */
+
+/* A lattice too large for one GPU splits along the flow axis into slabs, one per GPU, each a
+ * lattice whose faces towards its neighbours are cuts (mfc_lattice_desc.cut).  After every step,
+ * each slab packs the populations that leave it through a cut face and the neighbour unpacks them
+ * into its ghost layer, where its next step pulls them; the check sums of a step are summed over
+ * the slabs (FP64) before the residual test.  Side 0 is the low face of the flow axis, side 1 the
+ * high face.  The population values cross in their storage type (FP32, FP16 or FP64), so a slab
+ * run computes exactly what the whole lattice computes.  Buffers are device memory of the caller,
+ * used in stream order on the lattice stream. */
+
+/* Bytes of the halo of one side: (crossing flow planes + crossing transport planes) x the nodes of
+ * a cross-section x the storage size. */
+MFC_API mfc_status mfc_halo_bytes(mfc_lattice *lat, int side, size_t *bytes);
+/* Queue the copy of the populations leaving through face `side` (the current state of the layer
+ * next to it) into dev_buf, direction-major then cross-section in node order. */
+MFC_API mfc_status mfc_halo_pack(mfc_lattice *lat, int side, void *dev_buf);
+/* Queue the copy of a neighbour's packed populations (its opposite side) into the ghost layer
+ * beyond face `side`, with the periodic images of the cross axes. */
+MFC_API mfc_status mfc_halo_unpack(mfc_lattice *lat, int side, const void *dev_buf);
+/* Node classes of the neighbour's layer next to face `side` (host, one cross-section: ny bytes in
+ * 2-D, nx*ny in 3-D): they decide which links across the cut bounce back (Eq. 11).  Rebuilds the
+ * link masks (warm start).  Before the first call a cut sees open nodes.  Blocks. */
+MFC_API mfc_status mfc_set_halo_classes(mfc_lattice *lat, int side, const uint8_t *plane);
+/* nsteps fused steps, the last one a check step; sums[9] (host) receives that step's FP64 sums
+ * over this lattice: sum |u - u_prev|^2, sum |u|^2, sum rho, sum (C - C_prev)^2, sum C^2, sum C,
+ * the consumption, the count of non-finite values and the count of nodes outside the range of
+ * the scheme (u_prev, C_prev: the fields of the previous check or stepping call).  Blocks. */
+MFC_API mfc_status mfc_step_check_sums(mfc_lattice *lat, int nsteps, double *sums);
 
 /* ---- sums without allocation ------------------------------------------------------------ */
 

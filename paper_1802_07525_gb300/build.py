@@ -23,7 +23,7 @@ LIB = os.path.join(OUT_DIR, "libmfc.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 SOURCES = ["lbm2d_f32.cu", "lbm2d_f16.cu", "lbm3d_f32.cu", "lbm3d_f16.cu", "lbm2d9_f32.cu",
            "lbm2d9_f16.cu", "lbm2d_f64.cu", "lbm3d_f64.cu", "lbm2d9_f64.cu", "runtime.cu", "batch.cu",
-           "noalloc.cu", "electro.cu", "agent.cu"]
+           "noalloc.cu", "electro.cu", "agent.cu", "slab.cu"]
 HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh", "lbm_aux.cuh", "lbm_launch.cuh", "mfc_internal.h",
            "runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

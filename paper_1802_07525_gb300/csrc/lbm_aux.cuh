@@ -65,7 +65,8 @@ __device__ __forceinline__ void node_xyz(const Geo &g, long long q, int *x, int 
 
 // Is the link that brings a population along (cx,cy,cz) to (x,y,z) blocked (Eq. 11)?  Walls win
 // over the inlet and outlet; a periodic source wraps; an outlet source moves back onto the last
-// layer, whose class decides.
+// layer, whose class decides; a source beyond a cut is the neighbouring slab's node, whose class
+// the halo plane gives.
 template <int DIM>
 __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, int z, int cx, int cy,
                                              int cz, uint8_t bit)
@@ -73,18 +74,27 @@ __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, in
     int s[3] = {x - cx, y - cy, z - cz};
     const int n[3] = {m.geo.nx, m.geo.ny, m.geo.nz};
     constexpr int FA = DIM == 2 ? 0 : 2;
+    const int side = s[FA] < 0 ? 0 : (s[FA] >= n[FA] ? 1 : -1);
+    const bool across_cut = side >= 0 && m.cut[side];
     for (int ax = 0; ax < DIM; ++ax) {
         const bool out = s[ax] < 0 || s[ax] >= n[ax];
+        if (ax == FA && across_cut) continue;
         if (out && !(m.bc[ax] == BC_PERIODIC || (m.bc[ax] == BC_INOUT && ax == FA))) return true;
     }
     for (int ax = 0; ax < DIM; ++ax) {
         if (s[ax] >= 0 && s[ax] < n[ax]) continue;
+        if (ax == FA && across_cut) continue;
         if (m.bc[ax] == BC_PERIODIC) {
             s[ax] = s[ax] < 0 ? s[ax] + n[ax] : s[ax] - n[ax];
         } else {
             if (s[ax] < 0) return false;  // inlet ghost
             s[ax] = n[ax] - 1;            // outlet: the last layer decides
         }
+    }
+    if (across_cut) {
+        const uint8_t *h = m.halo_cls[side];
+        const long long cross = DIM == 2 ? (long long)s[1] : s[0] + (long long)m.geo.nx * s[1];
+        return h && (h[cross] & bit) != 0;
     }
     return (m.cls_new[s[0] + (long long)m.geo.nx * (s[1] + (long long)m.geo.ny * s[2])] & bit) != 0;
 }
@@ -137,8 +147,14 @@ template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kerne
             for (int ax = 0; ax < DIM; ++ax) store_field(m.fld_u, m.dbl, ax * m.geo.plane + k, 0.0);
         }
         if (m.reset || !a_open) store_field(m.fld_c, m.dbl, k, -(double)m.c_ref);
-        if (f_open) atomicAdd(&m.counts[0], 1ull);
-        if (a_open) atomicAdd(&m.counts[1], 1ull);
+        // open-node counts: one atomic per warp (one per node serialises on the two counters,
+        // milliseconds on a lattice of millions of nodes)
+        const unsigned act = __activemask();
+        const unsigned fo = __ballot_sync(act, f_open), ao = __ballot_sync(act, a_open);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+            if (fo) atomicAdd(&m.counts[0], (unsigned long long)__popc(fo));
+            if (ao) atomicAdd(&m.counts[1], (unsigned long long)__popc(ao));
+        }
     }
 }
 

@@ -76,6 +76,7 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     R rho_out;            // outlet density
     R c_ref;              // offset of the stored transport populations
     int ade_dirichlet;    // transport outlet: 0 zero-gradient, 1 Dirichlet
+    int cut[2];           // the low / high face of the flow axis is a cut to a neighbouring slab
     R bb_in[QF];          // moving-wall inlet term 2 w_i rho_in (c_i . u_in) / cs^2
     R gin_dev[QA];        // inlet ghost: w_i c_in (1 + c_i . u_in / cs^2) - w_i c_ref
     R gout_dev[QA];       // Dirichlet outlet ghost at c_out, same form
@@ -239,12 +240,12 @@ __device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *
         }
         if (!inout) continue;
         const int cf = F::c(i, FA);
-        if (p[FA] == 0 && cf == 1 && !((L >> i) & 1u)) {  // inlet: the node's own next-step pull
+        if (p[FA] == 0 && cf == 1 && !a.cut[0] && !((L >> i) & 1u)) {  // inlet: the node's own next-step pull
             const int q0 = x - F::c(i, 0), q1 = y - F::c(i, 1), q2 = z - F::c(i, 2);
             st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2),
                ldplain(pop + (long long)F::opp(i) * a.geo.plane + k) + a.bb_in[i]);
         }
-        if (p[FA] == n[FA] - 1 && cf == -1) {  // outlet ghost fed by this last-layer node
+        if (p[FA] == n[FA] - 1 && cf == -1 && !a.cut[1]) {  // outlet ghost fed by this last-layer node
             const R cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
             const R v = weight<F, R>(i) * (a.rho_out - R(1) +
                                        a.rho_out * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
@@ -282,11 +283,11 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *p
         ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, x, y, z, false, ei, LazyGhosts<DIM, ST>::value ? own : nullptr);
         if (!inout) continue;
         const int cf = A::c(i, FA);
-        if (p[FA] == 0 && cf == 1 && !((L >> (Links<DIM, AQ>::ADE_SELF + i)) & 1u)) {
+        if (p[FA] == 0 && cf == 1 && !a.cut[0] && !((L >> (Links<DIM, AQ>::ADE_SELF + i)) & 1u)) {
             const int q0 = x - A::c(i, 0), q1 = y - A::c(i, 1), q2 = z - A::c(i, 2);
             st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2), a.gin_dev[i]);
         }
-        if (p[FA] == n[FA] - 1 && cf == -1) {
+        if (p[FA] == n[FA] - 1 && cf == -1 && !a.cut[1]) {
             int b[3] = {x, y, z};
             b[FA] = n[FA];
             if (a.ade_dirichlet) ghost_images<DIM, A, ST>(a.geo, a.bc, pop, i, b[0], b[1], b[2], true, a.gout_dev[i]);
@@ -342,7 +343,7 @@ __device__ __forceinline__ void flow_ghosts_step(const StepArgs<DIM, ST, AQ> &a,
             ghost_images<DIM, F, ST>(a.geo, a.bc, pop, i, x, y, z, false, di);
         }
     }
-    if (a.bc[FA] == BC_INOUT && p[FA] == n[FA] - 1) {
+    if (a.bc[FA] == BC_INOUT && p[FA] == n[FA] - 1 && !a.cut[1]) {
         const R uv[3] = {u0, u1, DIM == 3 ? u2 : R(0)};
         const R uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
 #pragma unroll
@@ -455,8 +456,8 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     constexpr int FA = flow_axis<DIM>();
     const int pf = FA == 0 ? x : z;
     const bool inout = READER && bnd_tile && a.bc[FA] == BC_INOUT;
-    const bool at_in = inout && pf == 0;
-    const bool at_out = inout && pf == (FA == 0 ? g.nx : g.nz) - 1;
+    const bool at_in = inout && pf == 0 && !a.cut[0];
+    const bool at_out = inout && pf == (FA == 0 ? g.nx : g.nz) - 1 && !a.cut[1];
     // How a bounce-back population is fetched.  Unconditional own-opposite loads, selected
     // afterwards, keep every load independent of the link word (2-D: measured faster in FP32
     // and FP16); in 3-D (19 + 7 directions under tight register caps) one load per direction from
@@ -804,6 +805,8 @@ struct MaskArgs {
     void *fld_rho, *fld_u, *fld_c;
     float c_ref;
     unsigned long long *counts;  // [0] flow-open nodes, [1] transport-open nodes
+    int cut[2];                  // the low / high face of the flow axis is a cut
+    const uint8_t *halo_cls[2];  // the neighbour's classes next to each cut (null: open)
 };
 
 struct ConvArgs {

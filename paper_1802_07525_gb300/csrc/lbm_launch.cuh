@@ -68,6 +68,8 @@ Args make_args(const StepHost &h)
     a.partials = h.partials;
     a.omega = (R)h.omega; a.omega_c = (R)h.omega_c; a.k_sink = (R)h.k_sink; a.u_scale = (R)h.u_scale;
     a.rho_out = (R)h.rho_out; a.c_ref = (R)h.c_ref; a.ade_dirichlet = h.ade_dirichlet;
+    a.cut[0] = h.cut[0];
+    a.cut[1] = h.cut[1];
     a.k_half = (R)h.k_half;
     for (int i = 0; i < Args::QF; ++i) a.bb_in[i] = (R)h.bb_in[i];
     for (int i = 0; i < Args::QA; ++i) {

@@ -35,6 +35,7 @@ struct StepHost {
     double omega, omega_c, k_sink, u_scale, rho_out, c_ref;
     double k_half;  // half-saturation concentration of the consumption (0: first order)
     int ade_dirichlet;
+    int cut[2];  // the low / high face of the flow axis is a cut (slab decomposition)
     double bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
 };
 

@@ -171,6 +171,15 @@ mfc_status check_desc(const mfc_lattice_desc *d, std::string *why)
         *why = "ade_q must be 0 (default), 5 or 9 in 2-D, 7 in 3-D";
         return MFC_ERR_ARG;
     }
+    for (int s = 0; s < 2; ++s)
+        if (d->cut[s] != 0 && d->cut[s] != 1) {
+            *why = "cut[] must be 0 or 1";
+            return MFC_ERR_ARG;
+        }
+    if ((d->cut[0] || d->cut[1]) && d->bc[fa] == MFC_BC_PERIODIC) {
+        *why = "a lattice with a cut may not be periodic along the flow axis";
+        return MFC_ERR_ARG;
+    }
     return MFC_OK;
 }
 
@@ -259,6 +268,8 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->rho_out = p.rho_out;
     h->c_ref = L->c_ref;
     h->ade_dirichlet = p.ade_outlet == MFC_OUTLET_DIRICHLET;
+    h->cut[0] = L->desc.cut[0];
+    h->cut[1] = L->desc.cut[1];
     const int fa = L->dim == 2 ? 0 : 2;
     for (int i = 0; i < L->qf; ++i) {
         const int ci = L->dim == 2 ? FlowSet<2>::c(i, fa) : FlowSet<3>::c(i, fa);
@@ -504,6 +515,8 @@ void release(mfc_lattice *L)
     dev_free(L, L->counts_d);
     dev_free(L, L->staging);
     dev_free(L, L->biomass);
+    dev_free(L, L->halo_cls[0]);
+    dev_free(L, L->halo_cls[1]);
     dev_free(L, L->agent_keys);
     dev_free(L, L->agent_list);
     dev_free(L, L->agent_mark);
@@ -545,6 +558,10 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
     m.fld_rho = L->fld_rho; m.fld_u = L->fld_u; m.fld_c = L->fld_c;
     m.c_ref = L->c_ref;
     m.counts = L->counts_d;
+    for (int s = 0; s < 2; ++s) {
+        m.cut[s] = L->desc.cut[s];
+        m.halo_cls[s] = L->halo_cls[s];
+    }
     CK(L, cudaMemsetAsync(L->counts_d, 0, 2 * sizeof(unsigned long long), L->stream));
     CK(L, launch_links(L->dim, L->qa, m, L->stream));
     mfc_status st = fill_ghosts(L);
@@ -846,6 +863,38 @@ MFC_API mfc_status mfc_solve_steady(mfc_lattice *L, const mfc_solve_opts *opts, 
     r.status = st;
     if (out) *out = r;
     return st;
+}
+
+MFC_API mfc_status mfc_step_check_sums(mfc_lattice *L, int nsteps, double *sums)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (nsteps < 1 || !sums) return fail(L, MFC_ERR_ARG, "nsteps must be >= 1 and sums non-NULL");
+    st = enqueue_block(L, KIND_COUPLED, nsteps, true);
+    if (st != MFC_OK) return st;
+    CK(L, cudaStreamSynchronize(L->stream));
+    for (int m = 0; m < NSUM; ++m) sums[m] = L->results_h[m];
+    L->last_current = L->results_h[SUM_CURRENT];
+    return MFC_OK;
+}
+
+MFC_API mfc_status mfc_set_halo_classes(mfc_lattice *L, int side, const uint8_t *plane)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if ((side != 0 && side != 1) || !plane) return fail(L, MFC_ERR_ARG, "side must be 0 or 1, plane non-NULL");
+    if (!L->desc.cut[side]) return fail(L, MFC_ERR_STATE, "that face is not a cut");
+    const size_t n = L->dim == 2 ? (size_t)L->ny : (size_t)L->nx * L->ny;
+    for (size_t q = 0; q < n; ++q)
+        if (plane[q] > 7) return fail(L, MFC_ERR_ARG, "class values above 7");
+    if (!L->halo_cls[side]) {
+        void *p = nullptr;
+        if (!dev_alloc(L, &p, round_up(n, 256))) return fail(L, MFC_ERR_OOM, "halo classes: allocation failed");
+        L->halo_cls[side] = static_cast<uint8_t *>(p);
+        L->bytes += round_up(n, 256);
+    }
+    CK(L, cudaMemcpyAsync(L->halo_cls[side], plane, n, cudaMemcpyHostToDevice, L->stream));
+    return apply_geometry(L, L->cls_cur, 0);
 }
 
 MFC_API mfc_status mfc_biofilm_grow(mfc_lattice *L, uint64_t seed, uint64_t cycle, double prob,

@@ -51,6 +51,8 @@ struct mfc_lattice {
     int grid = 1, block = mfc::DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
     int offsets32 = 1;  // plain steps with 32-bit element offsets where the arrays allow
 
+    // slab decomposition: the neighbours' classes next to the cut faces (device planes, or null)
+    uint8_t *halo_cls[2] = {nullptr, nullptr};
     // agent-based biofilm (allocated by the first mfc_agent_step or mfc_write_biomass)
     double *biomass = nullptr;                // C^bio per node, dense (x fastest)
     unsigned long long *agent_keys = nullptr; // attachment keys per node

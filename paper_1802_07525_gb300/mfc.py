@@ -32,7 +32,7 @@ MFC_POP_FLOW, MFC_POP_ADE, MFC_FIELD_VELOCITY = 0, 1, 2
 class LatticeDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int),
-                ("ade_q", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("ade_q", ctypes.c_int), ("cut", ctypes.c_int * 2), ("stream", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -162,6 +162,11 @@ _SIGS = {
                                       ctypes.POINTER(AgentStats)]),
     "mfc_read_biomass": (ctypes.c_int, [_vp, _dp]),
     "mfc_write_biomass": (ctypes.c_int, [_vp, _dp]),
+    "mfc_halo_bytes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "mfc_halo_pack": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "mfc_halo_unpack": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "mfc_set_halo_classes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8)]),
+    "mfc_step_check_sums": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "mfc_electro_default_params": (ctypes.c_int, [ctypes.POINTER(ElectroParams)]),
     "mfc_electro_update": (ctypes.c_int, [ctypes.POINTER(ElectroParams), ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double,
@@ -229,7 +234,7 @@ def make_params(tau=0.8, tau_c=0.7, u_in=0.01, rho_in=1.0, rho_out=1.0, c_in=1.0
     return Params(tau, tau_c, u_in, rho_in, rho_out, c_in, c_out, k_sink, u_scale, ade_outlet, k_half)
 
 
-def make_desc(shape, bc=None, precision=MFC_FP32, stream=None, ade_q=0) -> LatticeDesc:
+def make_desc(shape, bc=None, precision=MFC_FP32, stream=None, ade_q=0, cut=(0, 0)) -> LatticeDesc:
     shape = tuple(int(s) for s in shape)
     dim = len(shape)
     if bc is None:
@@ -243,6 +248,7 @@ def make_desc(shape, bc=None, precision=MFC_FP32, stream=None, ade_q=0) -> Latti
         d.bc[a] = bcs[a]
     d.precision = precision
     d.ade_q = ade_q
+    d.cut[0], d.cut[1] = int(cut[0]), int(cut[1])
     d.stream = stream
     return d
 
@@ -254,16 +260,18 @@ def lattice_bytes(shape, bc=None, precision=MFC_FP32, ade_q=0) -> int:
 class Lattice:
     """One lattice resident on the current CUDA device (see ``include/mfc.h``)."""
 
-    def __init__(self, shape, *, bc=None, precision=MFC_FP32, stream=None, ade_q=0, **params):
+    def __init__(self, shape, *, bc=None, precision=MFC_FP32, stream=None, ade_q=0, cut=(0, 0),
+                 **params):
         """ade_q: 0 for the default transport set (D2Q5 / D3Q7), 9 for D2Q9 with the equilibrium
-        of Eq. 5 (2-D)."""
+        of Eq. 5 (2-D).  cut: the low / high faces of the flow axis that are cuts to neighbouring
+        slabs."""
         self.shape = tuple(int(s) for s in shape)
         self.dim = len(self.shape)
         self.N = int(np.prod(self.shape))
         self.qf = 9 if self.dim == 2 else 19
         self.qa = (9 if ade_q == 9 else 5) if self.dim == 2 else 7
         self._L = lib()
-        self.desc = make_desc(self.shape, bc, precision, stream, ade_q)
+        self.desc = make_desc(self.shape, bc, precision, stream, ade_q, cut)
         self.params = make_params(**params)
         h = ctypes.c_void_p()
         st = self._L.mfc_create_lattice(ctypes.byref(self.desc), ctypes.byref(self.params),
@@ -329,6 +337,31 @@ class Lattice:
         self._check(self._L.mfc_biofilm_grow(self.handle, seed, cycle, prob, c_thresh,
                                              ctypes.byref(n)))
         return int(n.value)
+
+    # ---- slab decomposition ----------------------------------------------------------------
+
+    def halo_bytes(self, side: int) -> int:
+        n = ctypes.c_size_t()
+        self._check(self._L.mfc_halo_bytes(self.handle, side, ctypes.byref(n)))
+        return int(n.value)
+
+    def halo_pack(self, side: int, dev_ptr: int):
+        """Queue the populations leaving through face `side` into device memory at dev_ptr."""
+        self._check(self._L.mfc_halo_pack(self.handle, side, ctypes.c_void_p(dev_ptr)))
+
+    def halo_unpack(self, side: int, dev_ptr: int):
+        """Queue a neighbour's packed populations into the ghost layer beyond face `side`."""
+        self._check(self._L.mfc_halo_unpack(self.handle, side, ctypes.c_void_p(dev_ptr)))
+
+    def set_halo_classes(self, side: int, plane):
+        p = np.ascontiguousarray(np.asarray(plane, np.uint8).reshape(-1))
+        self._check(self._L.mfc_set_halo_classes(self.handle, side, _ptr(p, ctypes.c_uint8)))
+
+    def step_check_sums(self, nsteps: int = 1) -> np.ndarray:
+        """nsteps fused steps, the last a check step; its nine FP64 sums over this lattice."""
+        s = np.zeros(9)
+        self._check(self._L.mfc_step_check_sums(self.handle, nsteps, _ptr(s)))
+        return s
 
     def agent_step(self, params: AgentParams, cycle: int) -> dict:
         """One agent-based biofilm step (attachment, growth, spreading, class update)."""
