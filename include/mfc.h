@@ -66,10 +66,9 @@ typedef enum {
     MFC_ERR_STATE = 8,        /* call not valid in the object's current state */
     MFC_PENDING = 9,          /* a batch request has not finished yet */
     MFC_ERR_UNSTABLE = 10     /* at a check, a flow-open node moved at or above the lattice sound
-                                 speed (|u|^2 >= 1/3) or had a density outside (0, 2): the flow has
-                                 left the weakly compressible, low-Mach range of the BGK
-                                 equilibrium (Eq. 5) and the solve stops there, before it turns
-                                 non-finite */
+                                 speed (|u|^2 >= 1/3) or had rho <= 0: the flow has left the range
+                                 of the low-Mach BGK equilibrium (Eq. 5) and the solve stops there,
+                                 before it turns non-finite */
 } mfc_status;
 
 enum { MFC_BC_WALL = 0, MFC_BC_PERIODIC = 1, MFC_BC_INOUT = 2 };
@@ -173,8 +172,8 @@ MFC_API mfc_status mfc_step_coupled(mfc_lattice *lat, int nsteps);
 /* Iterate to steady state (Sec. 4: "enough time steps until an equilibrium is reached"),
  * checking the residuals every K steps with CUDA-graph replays of K steps.  Blocks.
  * Returns MFC_OK, MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_UNSTABLE (first check with a
- * node at or above the sound speed or with rho outside (0, 2)) or MFC_ERR_TIMEOUT; out
- * (optional) is filled in every case. */
+ * node at or above the sound speed or at rho <= 0) or MFC_ERR_TIMEOUT; out (optional) is
+ * filled in every case. */
 MFC_API mfc_status mfc_solve_steady(mfc_lattice *lat, const mfc_solve_opts *opts,
                                     mfc_solve_result *out);
 

@@ -545,10 +545,9 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 acc[SUM_U2] = u2;
                 acc[SUM_MASS] = R(1) + rp;
                 if (!isfinite(rp) || !isfinite(u2)) acc[SUM_BAD] = R(1);
-                // the BGK equilibrium is a low-Mach expansion of a weakly compressible flow: at or
-                // past the sound speed, or with the density outside (0, 2), the solve has left
-                // the scheme's range
-                if (R(3) * u2 >= R(1) || rp <= R(-1) || rp >= R(1)) acc[SUM_FAST] = R(1);
+                // the BGK equilibrium is a low-Mach expansion: at or past the sound speed, or at a
+                // non-positive density, the solve has left the scheme's range
+                if (R(3) * u2 >= R(1) || rp <= R(-1)) acc[SUM_FAST] = R(1);
             }
             a.fld_rho[k] = rp;
 #pragma unroll

@@ -162,7 +162,7 @@ enum : int {
     SUM_CURRENT = 6,// sum over consumption nodes of the consumption (k C, or k C K_s / (K_s + C))
     SUM_BAD = 7,    // count of non-finite values
     SUM_FAST = 8,   // count of flow-open nodes outside the scheme's range: |u|^2 >= cs^2 = 1/3
-                    // (the flow at or above the lattice sound speed), rho <= 0 or rho >= 2
+                    // (the flow at or above the lattice sound speed) or rho <= 0
     NSUM = 9
 };
 

@@ -1065,7 +1065,7 @@ MFC_API const char *mfc_status_string(mfc_status s)
     case MFC_ERR_CUDA: return "CUDA error";
     case MFC_NOT_CONVERGED: return "not converged within the step cap";
     case MFC_ERR_NONFINITE: return "non-finite residual, mass or current";
-    case MFC_ERR_UNSTABLE: return "flow at or above the lattice sound speed, or density outside (0, 2)";
+    case MFC_ERR_UNSTABLE: return "flow at or above the lattice sound speed, or non-positive density";
     case MFC_ERR_TIMEOUT: return "wall-clock limit reached";
     case MFC_ERR_STATE: return "invalid state";
     case MFC_PENDING: return "pending";

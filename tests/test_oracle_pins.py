@@ -697,7 +697,8 @@ def test_flow_at_the_sound_speed_stops_the_solve_at_the_first_check(dim):
 
 def test_range_guard_counts_fast_and_non_positive_density_nodes():
     """The count of the guard over hand-set fields: nodes with |u|^2 >= 1/3 (on the boundary
-    too) or a density outside (0, 2) among the flow-open nodes; blocked nodes never count."""
+    too) or rho <= 0 among the flow-open nodes; blocked nodes never count, nor does a high
+    density (the 128x64 channel's steady state has rho near 2 upstream of its block)."""
     shape = (8, 4)
     cls = np.zeros(32, np.uint8)
     cls[5] = FLOW_SOLID | ADE_SOLID
@@ -710,10 +711,8 @@ def test_range_guard_counts_fast_and_non_positive_density_nodes():
     o.rho[4] = 0.0                         # non-positive density
     o.u[0, 5] = 0.9                        # blocked: not counted
     o.rho[6] = 1e-12                       # small but positive
-    o.rho[7] = 1.999999                    # below 2
+    o.rho[7] = 2.5                         # high density: not out of range
     assert o.sums()[8] == 3
-    o.rho[7] = 2.0                         # the density doubled
-    assert o.sums()[8] == 4
 
 
 # ------------------------------------------------------------------------------------------
