@@ -374,6 +374,21 @@ MFC_API mfc_status mfc_set_halo_classes(mfc_lattice *lat, int side, const uint8_
  * the scheme (u_prev, C_prev: the fields of the previous check or stepping call).  Blocks. */
 MFC_API mfc_status mfc_step_check_sums(mfc_lattice *lat, int nsteps, double *sums);
 
+/* ---- checking builds ---------------------------------------------------------------------- */
+
+/* The library can be built with MFC_CHECK_BOUNDS (paper_1802_07525_gb300.build with
+ * check_bounds=True: _lib/libmfc_check.so), a debugging build standing in for a memory checker:
+ * the step kernels test every element offset against the array they address and record the first
+ * one out of range (the access goes to an unused element instead), which the next synchronising
+ * call on the lattice returns as MFC_ERR_CUDA with the kernel line and the offset; and every
+ * device buffer of a lattice sits between two 256-byte guard regions of a fixed pattern.
+ * mfc_check_build returns 1 in such a build, 0 otherwise. */
+MFC_API int mfc_check_build(void);
+/* Checking builds: *bad receives the number of guard bytes of the lattice's buffers that no longer
+ * hold their pattern (a write past the end or before the start of a buffer).  Other builds: 0.
+ * Blocks. */
+MFC_API mfc_status mfc_check_canaries(mfc_lattice *lat, long long *bad);
+
 /* ---- sums without allocation ------------------------------------------------------------ */
 
 /* For callers that cannot allocate device memory (code inside another framework's memory pool

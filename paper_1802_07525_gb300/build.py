@@ -1,9 +1,12 @@
 """Build the sm_103a shared library ``_lib/libmfc.so`` in-tree with nvcc.
 
 Each CUDA translation unit compiles in its own nvcc process (in parallel), then one link step
-makes the shared library.  Only ``-gencode arch=compute_103a,code=sm_103a`` is emitted.
+makes the shared library.  Only ``-gencode arch=compute_103a,code=sm_103a`` is emitted.  With
+``check_bounds`` the same sources build, with ``-DMFC_CHECK_BOUNDS``, into the debugging library
+``_lib/libmfc_check.so`` (element offsets checked in the step kernels, guard regions around every
+device buffer).
 
-    python -m paper_1802_07525_gb300.build [--force] [--ptxas-verbose]
+    python -m paper_1802_07525_gb300.build [--force] [--ptxas-verbose] [--check-bounds]
 """
 from __future__ import annotations
 
@@ -20,7 +23,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmfc.so")
+LIB_CHECK = os.path.join(OUT_DIR, "libmfc_check.so")
 OBJ_DIR = os.path.join(HERE, "_build")
+OBJ_DIR_CHECK = os.path.join(HERE, "_build_check")
 SOURCES = ["lbm2d_f32.cu", "lbm2d_f16.cu", "lbm3d_f32.cu", "lbm3d_f16.cu", "lbm2d9_f32.cu",
            "lbm2d9_f16.cu", "lbm2d_f64.cu", "lbm3d_f64.cu", "lbm2d9_f64.cu", "runtime.cu", "batch.cu",
            "noalloc.cu", "electro.cu", "agent.cu", "slab.cu"]
@@ -36,26 +41,28 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmfc")
 
 
-def _flags(verbose: bool, relative: bool = False):
+def _flags(verbose: bool, relative: bool = False, check_bounds: bool = False):
     """nvcc flags; with ``relative`` the include directories are named relative to the repository
     root, so that a digest of the flags is the same in every checkout."""
     inc = "include" if relative else os.path.join(ROOT, "include")
     src = os.path.relpath(CSRC, ROOT) if relative else CSRC
     f = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", inc, "-I", src] + ARCH
+    if check_bounds:
+        f += ["-DMFC_CHECK_BOUNDS"]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
 
 
-def _digest(verbose: bool) -> str:
+def _digest(verbose: bool, check_bounds: bool = False) -> str:
     h = hashlib.sha256()
     for name in SOURCES + HEADERS:
         with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(ROOT, "include", "mfc.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(_flags(verbose)).encode())
+    h.update(" ".join(_flags(verbose, check_bounds=check_bounds)).encode())
     return h.hexdigest()
 
 
@@ -75,21 +82,25 @@ def kernel_digest(tu: str) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, quiet: bool = True) -> str:
-    """Compile (if sources changed) and return the path of libmfc.so."""
+def build(force: bool = False, verbose: bool = False, quiet: bool = True,
+          check_bounds: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libmfc.so (libmfc_check.so with
+    check_bounds)."""
+    lib_path = LIB_CHECK if check_bounds else LIB
+    obj_dir = OBJ_DIR_CHECK if check_bounds else OBJ_DIR
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    stamp = os.path.join(OUT_DIR, "libmfc.sha256")
-    dig = _digest(verbose)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    os.makedirs(obj_dir, exist_ok=True)
+    stamp = lib_path.replace(".so", ".sha256")
+    dig = _digest(verbose, check_bounds)
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == dig:
-                return LIB
+                return lib_path
     cc = nvcc()
-    flags = _flags(verbose)
+    flags = _flags(verbose, check_bounds=check_bounds)
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -103,20 +114,21 @@ def build(force: bool = False, verbose: bool = False, quiet: bool = True) -> str
             if err:
                 sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["--cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(dig)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--ptxas-verbose", action="store_true")
+    ap.add_argument("--check-bounds", action="store_true")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.ptxas_verbose, quiet=False))
+    print(build(force=a.force, verbose=a.ptxas_verbose, quiet=False, check_bounds=a.check_bounds))

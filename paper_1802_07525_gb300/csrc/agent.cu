@@ -365,8 +365,7 @@ mfc_status ensure_agent(mfc_lattice *L, int max_walk)
     }
     if (max_walk + 2 > L->agent_path_cap) {
         if (L->agent_path) {
-            if (L->pool) cudaFreeAsync(L->agent_path, L->stream);
-            else cudaFree(L->agent_path);
+            lattice_free(L, L->agent_path);
             L->agent_path = nullptr;
         }
         const int cap = max_walk + 2 > 1026 ? max_walk + 2 : 1026;

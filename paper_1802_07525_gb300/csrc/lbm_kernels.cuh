@@ -77,6 +77,7 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
     R c_ref;              // offset of the stored transport populations
     int ade_dirichlet;    // transport outlet: 0 zero-gradient, 1 Dirichlet
     int cut[2];           // the low / high face of the flow axis is a cut to a neighbouring slab
+    unsigned long long *bounds_err;  // checking builds: the first out-of-range element offset
     R bb_in[QF];          // moving-wall inlet term 2 w_i rho_in (c_i . u_in) / cs^2
     R gin_dev[QA];        // inlet ghost: w_i c_in (1 + c_i . u_in / cs^2) - w_i c_ref
     R gout_dev[QA];       // Dirichlet outlet ghost at c_out, same form
@@ -85,6 +86,28 @@ template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct StepArgs {
 template <typename ST> using ArithT = typename Arith<ST>::T;
 
 template <int DIM> __host__ __device__ constexpr int flow_axis() { return DIM == 2 ? 0 : 2; }
+
+// Checking builds (MFC_CHECK_BOUNDS) test every element offset the step forms against the size
+// of the array it addresses; the first offset out of range is recorded (site and offset) and the
+// access goes to element 0, which lies in front of every node and ghost cell and is never read as
+// a population, so nothing outside the arrays is touched and the kernel runs on.  The library
+// reports the record as an error at its next synchronising call.  Other builds check nothing.
+#ifdef MFC_CHECK_BOUNDS
+template <typename IX>
+__device__ __forceinline__ IX bound_idx(IX idx, long long limit, unsigned long long *err, int site)
+{
+    if ((long long)idx < 0 || (long long)idx >= limit) {
+        if (err)
+            atomicCAS(err, 0ull, (1ull << 63) | ((unsigned long long)site << 40) |
+                                     ((unsigned long long)(long long)idx & 0xFFFFFFFFFFull));
+        return (IX)0;
+    }
+    return idx;
+}
+#define MFC_IDX(idx, limit) ::mfc::bound_idx((idx), (long long)(limit), a.bounds_err, __LINE__)
+#else
+#define MFC_IDX(idx, limit) (idx)
+#endif
 
 // A plain (coherent) load, for values this thread stored earlier in the same kernel.
 __device__ __forceinline__ float ldplain(const float *p) { return *p; }
@@ -242,8 +265,8 @@ __device__ __forceinline__ void flow_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *
         const int cf = F::c(i, FA);
         if (p[FA] == 0 && cf == 1 && !a.cut[0] && !((L >> i) & 1u)) {  // inlet: the node's own next-step pull
             const int q0 = x - F::c(i, 0), q1 = y - F::c(i, 1), q2 = z - F::c(i, 2);
-            st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2),
-               ldplain(pop + (long long)F::opp(i) * a.geo.plane + k) + a.bb_in[i]);
+            st(pop + MFC_IDX((long long)i * a.geo.plane + a.geo.at(q0, q1, q2), F::Q * a.geo.plane),
+               ldplain(pop + MFC_IDX((long long)F::opp(i) * a.geo.plane + k, F::Q * a.geo.plane)) + a.bb_in[i]);
         }
         if (p[FA] == n[FA] - 1 && cf == -1 && !a.cut[1]) {  // outlet ghost fed by this last-layer node
             const R cu = F::c(i, 0) * uv[0] + F::c(i, 1) * uv[1] + F::c(i, 2) * uv[2];
@@ -285,7 +308,7 @@ __device__ __forceinline__ void ade_ghosts(const StepArgs<DIM, ST, AQ> &a, ST *p
         const int cf = A::c(i, FA);
         if (p[FA] == 0 && cf == 1 && !a.cut[0] && !((L >> (Links<DIM, AQ>::ADE_SELF + i)) & 1u)) {
             const int q0 = x - A::c(i, 0), q1 = y - A::c(i, 1), q2 = z - A::c(i, 2);
-            st(pop + (long long)i * a.geo.plane + a.geo.at(q0, q1, q2), a.gin_dev[i]);
+            st(pop + MFC_IDX((long long)i * a.geo.plane + a.geo.at(q0, q1, q2), A::Q * a.geo.plane), a.gin_dev[i]);
         }
         if (p[FA] == n[FA] - 1 && cf == -1 && !a.cut[1]) {
             int b[3] = {x, y, z};
@@ -392,10 +415,14 @@ __device__ __forceinline__ bool tile_on_open_boundary(const Geo &g, const int (&
 // than at 32), FP32 2-D steps with D2Q9 transport, and 2-D store/check steps 40.  3-D steps are
 // latency-bound and gain from warps: FP32 with 5 blocks of 256 threads (51 registers: 148 us per
 // 256x128x128 step, against 211 us uncapped at 128 registers) and FP16 with 4 (64 registers:
-// 154 against 178 us); tighter caps spill and run slower.  The FP64 instantiation (a parity
-// reference, twice the registers per value) gets 128.
-template <int DIM, int MODE, typename ST = float, int AQ = default_aq<DIM>()> struct StepOccupancy {
+// 154 against 178 us); tighter caps spill and run slower.  With 32-bit offsets the FP16 3-D plain
+// step fits 48 registers without spills, and 5 blocks run it 6% faster (119.0 against 126.8 us);
+// the FP32 3-D one gains nothing from 6 blocks (138.9 against 139.5 us, with spills).  The FP64
+// instantiation (a parity reference, twice the registers per value) gets 128.
+template <int DIM, int MODE, typename ST = float, int AQ = default_aq<DIM>(), bool IDX32 = false>
+struct StepOccupancy {
     static constexpr int blocks =
+        (IDX32 && MODE == MODE_PLAIN && DIM == 3 && sizeof(ST) == 2) ? 5 :
         sizeof(ST) == 8 ? 2
                         : (DIM == 2 ? ((MODE == MODE_PLAIN && sizeof(ST) == 4 && AQ == 5) ? 8 : 6)
                                     : (sizeof(ST) == 4 ? 5 : 4));
@@ -445,7 +472,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     const bool valid = MODE != MODE_CHECK || x < g.nx;
     const IX k = (IX)g.row0 + (IX)z * (IX)g.zs + (IX)y * (IX)g.px + (IX)(x < g.nx ? x : g.nx - 1);
     const IX P = (IX)g.plane;
-    const uint32_t L = __ldg(a.link + k);
+    const uint32_t L = __ldg(a.link + MFC_IDX(k, P));
     constexpr bool READER = BFORM != B_WRITER;
     const bool bnd_tile = BFORM == B_WRITER ? tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z)
                                             : BFORM == B_BOUNDARY;
@@ -471,9 +498,9 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     if (MODE == MODE_CHECK) {
         if (FLOW) {
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) u_prev[ax] = ldplain(a.fld_u + ax * g.plane + k);
+            for (int ax = 0; ax < DIM; ++ax) u_prev[ax] = ldplain(a.fld_u + MFC_IDX(ax * g.plane + k, DIM * P));
         }
-        if (ADE) c_prev = ldplain(a.fld_c + k);
+        if (ADE) c_prev = ldplain(a.fld_c + MFC_IDX(k, P));
     }
 
     if (FLOW) {
@@ -486,14 +513,14 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const bool inj = F::c(i, FA) == 1 && at_in && !bb;
             if (SELECT_LOADS) {
                 const IX o = (bb || inj) ? (IX)F::opp(i) * P : (IX)i * P - off;
-                d[i] = ld(a.fsrc + (k + o));
+                d[i] = ld(a.fsrc + MFC_IDX(k + o, F::Q * P));
                 if (F::c(i, FA) == 1 && inj) d[i] += a.bb_in[i];
             } else {
-                const R src = ld(a.fsrc + ((IX)i * P + k - off));
+                const R src = ld(a.fsrc + MFC_IDX((IX)i * P + k - off, F::Q * P));
                 if (i == 0) {
                     d[0] = src;
                 } else {
-                    const R own = ld(a.fsrc + ((IX)F::opp(i) * P + k));
+                    const R own = ld(a.fsrc + MFC_IDX((IX)F::opp(i) * P + k, F::Q * P));
                     d[i] = bb ? own : src;
                     if (F::c(i, FA) == 1 && inj) d[i] = own + a.bb_in[i];
                 }
@@ -525,9 +552,9 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const R feq = weight<F, R>(i) * (rp + (R(1) + rp) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
             const R v = kept(a.fdst, d[i] + a.omega * (feq - d[i]));
             moved += v;
-            if (valid) st(a.fdst + ((IX)i * P + k), v);
+            if (valid) st(a.fdst + MFC_IDX((IX)i * P + k, F::Q * P), v);
         }
-        if (valid) st(a.fdst + k, rp - moved);
+        if (valid) st(a.fdst + MFC_IDX(k, F::Q * P), rp - moved);
         if (ghosts && open) {
             if constexpr (READER) flow_ghosts_step<DIM, ST>(a, a.fdst, x, y, z, k, u[0], u[1], u[2]);
             else flow_ghosts<DIM, ST>(a, a.fdst, x, y, z, k, L, u[0], u[1], u[2]);
@@ -549,9 +576,9 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 // non-positive density, the solve has left the scheme's range
                 if (R(3) * u2 >= R(1) || rp <= R(-1)) acc[SUM_FAST] = R(1);
             }
-            a.fld_rho[k] = rp;
+            a.fld_rho[MFC_IDX(k, P)] = rp;
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) a.fld_u[ax * g.plane + k] = u[ax];
+            for (int ax = 0; ax < DIM; ++ax) a.fld_u[MFC_IDX(ax * g.plane + k, DIM * P)] = u[ax];
         }
     }
 
@@ -561,7 +588,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             for (int ax = 0; ax < DIM; ++ax) u[ax] *= a.u_scale;  // 0 on flow-blocked nodes
         } else if (!(L & (1u << LK::FLOW_SELF))) {
 #pragma unroll
-            for (int ax = 0; ax < DIM; ++ax) u[ax] = a.fld_u[ax * g.plane + k] * a.u_scale;
+            for (int ax = 0; ax < DIM; ++ax) u[ax] = a.fld_u[MFC_IDX(ax * g.plane + k, DIM * P)] * a.u_scale;
         }
         R e[A::Q];
 #pragma unroll
@@ -574,15 +601,15 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const bool out_v = A::c(i, FA) == -1 && at_out && !bb;
             if (SELECT_LOADS) {
                 const IX o = bb ? (IX)A::opp(i) * P : (IX)i * P - (out_v ? (IX)0 : off);
-                e[i] = ld(a.gsrc + (k + o));
+                e[i] = ld(a.gsrc + MFC_IDX(k + o, A::Q * P));
             } else {
-                const R src = ld(a.gsrc + ((IX)i * P + k - off));
+                const R src = ld(a.gsrc + MFC_IDX((IX)i * P + k - off, A::Q * P));
                 if (i == 0) {
                     e[0] = src;
                 } else {
-                    const R own = ld(a.gsrc + ((IX)A::opp(i) * P + k));
+                    const R own = ld(a.gsrc + MFC_IDX((IX)A::opp(i) * P + k, A::Q * P));
                     e[i] = bb ? own : src;
-                    if (A::c(i, FA) == -1 && out_v) e[i] = ld(a.gsrc + ((IX)i * P + k));
+                    if (A::c(i, FA) == -1 && out_v) e[i] = ld(a.gsrc + MFC_IDX((IX)i * P + k, A::Q * P));
                 }
             }
             if (A::c(i, FA) == 1 && in_v) e[i] = a.gin_dev[i];
@@ -620,9 +647,9 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
             const R geq = weight<A, R>(i) * (cp + (a.c_ref + cp) * shape);
             const R v = kept(a.gdst, e[i] + a.omega_c * (geq - e[i]) - weight<A, R>(i) * sink);
             moved += v;
-            if (valid) st(a.gdst + ((IX)i * P + k), v);
+            if (valid) st(a.gdst + MFC_IDX((IX)i * P + k, A::Q * P), v);
         }
-        if (valid) st(a.gdst + k, cp - sink - moved);
+        if (valid) st(a.gdst + MFC_IDX(k, A::Q * P), cp - sink - moved);
         if (ghosts && open) {
             if constexpr (READER) ade_ghosts_step<DIM, ST>(a, a.gdst, x, y, z, k);
             else ade_ghosts<DIM, ST>(a, a.gdst, x, y, z, k, L);
@@ -641,7 +668,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
                 }
                 if (!isfinite(cp)) acc[SUM_BAD] += R(1);
             }
-            a.fld_c[k] = open ? cp : -a.c_ref;
+            a.fld_c[MFC_IDX(k, P)] = open ? cp : -a.c_ref;
         }
     }
 }
@@ -650,7 +677,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
 // partial per block on check steps.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int AQ = default_aq<DIM>(), int SINK = SINK_LINEAR,
           bool IDX32 = false>
-__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
+__global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ, IDX32>::blocks) lbm_step_kernel(const StepArgs<DIM, ST, AQ> a)
 {
     using IX = typename std::conditional<IDX32, int, long long>::type;
     using R = ArithT<ST>;

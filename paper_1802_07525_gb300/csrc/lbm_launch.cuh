@@ -70,6 +70,7 @@ Args make_args(const StepHost &h)
     a.rho_out = (R)h.rho_out; a.c_ref = (R)h.c_ref; a.ade_dirichlet = h.ade_dirichlet;
     a.cut[0] = h.cut[0];
     a.cut[1] = h.cut[1];
+    a.bounds_err = h.bounds_err;
     a.k_half = (R)h.k_half;
     for (int i = 0; i < Args::QF; ++i) a.bb_in[i] = (R)h.bb_in[i];
     for (int i = 0; i < Args::QA; ++i) {

@@ -36,6 +36,7 @@ struct StepHost {
     double k_half;  // half-saturation concentration of the consumption (0: first order)
     int ade_dirichlet;
     int cut[2];  // the low / high face of the flow axis is a cut (slab decomposition)
+    unsigned long long *bounds_err;  // checking builds: the lattice's out-of-range record
     double bb_in[19], gin_dev[9], gout_dev[9];  // per flow / transport direction (at most 19 / 9)
 };
 

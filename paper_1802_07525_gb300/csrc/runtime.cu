@@ -115,6 +115,25 @@ mfc_status enter(mfc_lattice *L)
     return MFC_OK;
 }
 
+// Checking builds: after the lattice stream was synchronised, report an out-of-range element
+// offset recorded by the step kernels (site: source line; the offset).  Other builds: nothing.
+mfc_status check_bounds(mfc_lattice *L)
+{
+#ifdef MFC_CHECK_BOUNDS
+    unsigned long long rec = 0;
+    CK(L, cudaMemcpy(&rec, L->bounds_err, sizeof rec, cudaMemcpyDeviceToHost));
+    if (rec) {
+        L->sticky = MFC_ERR_CUDA;
+        return fail(L, MFC_ERR_CUDA, "element offset out of range at kernel line " +
+                                         std::to_string((rec >> 40) & 0x7FFFFF) + ", offset " +
+                                         std::to_string((long long)(rec & 0xFFFFFFFFFFull)));
+    }
+#else
+    (void)L;
+#endif
+    return MFC_OK;
+}
+
 mfc_status check_params(const mfc_params *p, std::string *why)
 {
     auto fin = [](double v) { return isfinite(v) != 0; };
@@ -270,6 +289,7 @@ void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
     h->ade_dirichlet = p.ade_outlet == MFC_OUTLET_DIRICHLET;
     h->cut[0] = L->desc.cut[0];
     h->cut[1] = L->desc.cut[1];
+    h->bounds_err = L->bounds_err;
     const int fa = L->dim == 2 ? 0 : 2;
     for (int i = 0; i < L->qf; ++i) {
         const int ci = L->dim == 2 ? FlowSet<2>::c(i, fa) : FlowSet<3>::c(i, fa);
@@ -466,34 +486,61 @@ mfc_status run_phase(mfc_lattice *L, int kind, double tol_flow, double tol_ade, 
 
 // Device allocation of a lattice buffer, zero-filled (ghosts and padding start defined): from
 // the lattice's pool on its stream, or with cudaMalloc.
+#ifdef MFC_CHECK_BOUNDS
+// Checking builds: every buffer sits between two guard regions of a known byte pattern, which
+// mfc_check_canaries compares after the fact.
+constexpr size_t GUARD = 256;
+constexpr unsigned char GUARD_BYTE = 0xA5;
+#else
+constexpr size_t GUARD = 0;
+#endif
+
 bool dev_alloc(mfc_lattice *L, void **p, size_t bytes)
 {
     *p = nullptr;
+    const size_t body = GUARD ? round_up(bytes, GUARD) : bytes;
+    const size_t total = body + 2 * GUARD;
+    void *base = nullptr;
     if (L->pool) {
-        if (cudaMallocFromPoolAsync(p, bytes, L->pool, L->stream) != cudaSuccess ||
-            cudaMemsetAsync(*p, 0, bytes, L->stream) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&base, total, L->pool, L->stream) != cudaSuccess ||
+            cudaMemsetAsync(base, 0, total, L->stream) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        return true;
+    } else {
+        if (cudaMalloc(&base, total) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (cudaMemset(base, 0, total) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
     }
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return false;
-    }
-    if (cudaMemset(*p, 0, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
+#ifdef MFC_CHECK_BOUNDS
+    char *b = static_cast<char *>(base);
+    cudaMemsetAsync(b, GUARD_BYTE, GUARD, L->stream);
+    cudaMemsetAsync(b + GUARD + body, GUARD_BYTE, GUARD, L->stream);
+    if (!L->pool) cudaStreamSynchronize(L->stream);
+    L->guards.push_back({b, body});
+#endif
+    *p = static_cast<char *>(base) + GUARD;
     return true;
 }
 
 void dev_free(mfc_lattice *L, void *p)
 {
     if (!p) return;
-    if (L->pool) cudaFreeAsync(p, L->stream);
-    else cudaFree(p);
+    char *base = static_cast<char *>(p) - GUARD;
+#ifdef MFC_CHECK_BOUNDS
+    for (size_t i = 0; i < L->guards.size(); ++i)
+        if (L->guards[i].first == base) {
+            L->guards.erase(L->guards.begin() + (long)i);
+            break;
+        }
+#endif
+    if (L->pool) cudaFreeAsync(base, L->stream);
+    else cudaFree(base);
 }
 
 void release(mfc_lattice *L)
@@ -514,6 +561,7 @@ void release(mfc_lattice *L)
     dev_free(L, L->results_d);
     dev_free(L, L->counts_d);
     dev_free(L, L->staging);
+    dev_free(L, L->bounds_err);
     dev_free(L, L->biomass);
     dev_free(L, L->halo_cls[0]);
     dev_free(L, L->halo_cls[1]);
@@ -585,6 +633,7 @@ mfc_status apply_geometry(mfc_lattice *L, const uint8_t *dev_cls_new, int reset)
 mfc_status mfc::lattice_enter(mfc_lattice *L) { return enter(L); }
 mfc_status mfc::lattice_fail(mfc_lattice *L, mfc_status s, const std::string &msg) { return fail(L, s, msg); }
 bool mfc::lattice_alloc(mfc_lattice *L, void **p, size_t bytes) { return dev_alloc(L, p, bytes); }
+void mfc::lattice_free(mfc_lattice *L, void *p) { dev_free(L, p); }
 mfc_status mfc::lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, int reset)
 {
     return apply_geometry(L, dev_cls, reset);
@@ -707,6 +756,9 @@ mfc_status mfc::lattice_create(const mfc_lattice_desc *desc, const mfc_params *p
     ok = ok && dalloc((void **)&L->partials, ((size_t)L->max_blocks + FINAL_STAGE1_MAX) * NSUM * sizeof(double));
     ok = ok && dalloc((void **)&L->results_d, NRESULT * sizeof(double));
     ok = ok && dalloc((void **)&L->counts_d, 2 * sizeof(unsigned long long));
+#ifdef MFC_CHECK_BOUNDS
+    ok = ok && dalloc((void **)&L->bounds_err, sizeof(unsigned long long));
+#endif
     if (!ok) {
         release(L);
         delete L;
@@ -859,6 +911,10 @@ MFC_API mfc_status mfc_solve_steady(mfc_lattice *L, const mfc_solve_opts *opts, 
     }
     r.current = L->results_h[SUM_CURRENT];
     r.substrate = L->results_h[SUM_C];
+    if (st != MFC_ERR_CUDA) {
+        const mfc_status bs = check_bounds(L);
+        if (bs != MFC_OK) st = bs;
+    }
     if (st == MFC_OK && !(conv_f && conv_a)) st = MFC_NOT_CONVERGED;
     r.status = st;
     if (out) *out = r;
@@ -873,6 +929,8 @@ MFC_API mfc_status mfc_step_check_sums(mfc_lattice *L, int nsteps, double *sums)
     st = enqueue_block(L, KIND_COUPLED, nsteps, true);
     if (st != MFC_OK) return st;
     CK(L, cudaStreamSynchronize(L->stream));
+    st = check_bounds(L);
+    if (st != MFC_OK) return st;
     for (int m = 0; m < NSUM; ++m) sums[m] = L->results_h[m];
     L->last_current = L->results_h[SUM_CURRENT];
     return MFC_OK;
@@ -936,6 +994,8 @@ MFC_API mfc_status mfc_read_fields(mfc_lattice *L, double *rho, double *u, doubl
     st = lattice_fields_async(L, rho, u, c);
     if (st != MFC_OK) return st;
     CK(L, cudaStreamSynchronize(L->stream));
+    st = check_bounds(L);
+    if (st != MFC_OK) return st;
     if (current) *current = L->last_current;
     return MFC_OK;
 }
@@ -996,7 +1056,7 @@ static mfc_status pop_io(mfc_lattice *L, int which, double *host_out, const doub
         if (st != MFC_OK) return st;
     }
     CK(L, cudaStreamSynchronize(L->stream));
-    return MFC_OK;
+    return check_bounds(L);
 }
 
 MFC_API mfc_status mfc_read_populations(mfc_lattice *L, int which, double *host)
@@ -1014,7 +1074,50 @@ MFC_API mfc_status mfc_synchronize(mfc_lattice *L)
     mfc_status st = enter(L);
     if (st != MFC_OK) return st;
     CK(L, cudaStreamSynchronize(L->stream));
+    return check_bounds(L);
+}
+
+#ifdef MFC_CHECK_BOUNDS
+// Bytes of the guard regions [p, p + n) that differ from the pattern, added to *bad.
+__global__ void guard_count_kernel(const unsigned char *p, size_t n, unsigned long long *bad)
+{
+    unsigned long long c = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c += p[i] != GUARD_BYTE;
+    if (c) atomicAdd(bad, c);
+}
+#endif
+
+MFC_API mfc_status mfc_check_canaries(mfc_lattice *L, long long *bad)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (!bad) return fail(L, MFC_ERR_ARG, "bad is NULL");
+    *bad = 0;
+#ifdef MFC_CHECK_BOUNDS
+    CK(L, cudaStreamSynchronize(L->stream));
+    CK(L, cudaMemsetAsync(L->counts_d, 0, sizeof(unsigned long long), L->stream));
+    for (auto &g : L->guards) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(g.first);
+        guard_count_kernel<<<1, 256, 0, L->stream>>>(b, GUARD, L->counts_d);
+        guard_count_kernel<<<1, 256, 0, L->stream>>>(b + GUARD + g.second, GUARD, L->counts_d);
+    }
+    CK(L, cudaGetLastError());
+    unsigned long long n = 0;
+    CK(L, cudaMemcpyAsync(&n, L->counts_d, sizeof n, cudaMemcpyDeviceToHost, L->stream));
+    CK(L, cudaStreamSynchronize(L->stream));
+    *bad = (long long)n;
+#endif
     return MFC_OK;
+}
+
+MFC_API int mfc_check_build(void)
+{
+#ifdef MFC_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 MFC_API mfc_status mfc_set_launch(mfc_lattice *L, const mfc_launch *v)

@@ -51,6 +51,10 @@ struct mfc_lattice {
     int grid = 1, block = mfc::DEFAULT_BLOCK, nblocks = 1, max_blocks = 1;
     int offsets32 = 1;  // plain steps with 32-bit element offsets where the arrays allow
 
+    // checking builds (MFC_CHECK_BOUNDS): the out-of-range record of the step kernels, and the
+    // guard regions around every device buffer (allocation base, bytes between the guards)
+    unsigned long long *bounds_err = nullptr;
+    std::vector<std::pair<char *, size_t>> guards;
     // slab decomposition: the neighbours' classes next to the cut faces (device planes, or null)
     uint8_t *halo_cls[2] = {nullptr, nullptr};
     // agent-based biofilm (allocated by the first mfc_agent_step or mfc_write_biomass)
@@ -89,6 +93,7 @@ mfc_status lattice_fail(mfc_lattice *L, mfc_status s, const std::string &msg);
 // Zero-filled device allocation on the lattice's stream (false when it fails); freed with the
 // lattice.
 bool lattice_alloc(mfc_lattice *L, void **p, size_t bytes);
+void lattice_free(mfc_lattice *L, void *p);
 // Replace the node classes by the device array dev_cls (N bytes) and rebuild the link masks;
 // reset != 0 returns every open node to rest, else a warm start.  Blocks.
 mfc_status lattice_apply_classes(mfc_lattice *L, const uint8_t *dev_cls, int reset);

@@ -17,7 +17,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libmfc.so")
+# MFC_LIBRARY=check selects the checking build (element offsets and guard regions checked)
+LIB_PATH = os.path.join(_HERE, "_lib", "libmfc_check.so" if os.environ.get("MFC_LIBRARY") == "check"
+                        else "libmfc.so")
 
 MFC_OK, MFC_ERR_ARG, MFC_ERR_OOM, MFC_ERR_OOM_BUDGET, MFC_ERR_CUDA = 0, 1, 2, 3, 4
 MFC_NOT_CONVERGED, MFC_ERR_NONFINITE, MFC_ERR_TIMEOUT, MFC_ERR_STATE, MFC_PENDING = 5, 6, 7, 8, 9
@@ -156,6 +158,8 @@ _SIGS = {
     "mfc_synchronize": (ctypes.c_int, [_vp]),
     "mfc_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
     "mfc_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(Launch)]),
+    "mfc_check_build": (ctypes.c_int, []),
+    "mfc_check_canaries": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mfc_field_sums_noalloc": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_double, _vp, _vp]),
     "mfc_agent_step": (ctypes.c_int, [_vp, ctypes.POINTER(AgentParams), ctypes.c_uint64,
@@ -406,6 +410,12 @@ class Lattice:
         v = Launch()
         self._check(self._L.mfc_get_launch(self.handle, ctypes.byref(v)))
         return v.as_dict()
+
+    def check_canaries(self) -> int:
+        """Guard bytes found changed (checking builds; 0 in other builds)."""
+        n = ctypes.c_longlong()
+        self._check(self._L.mfc_check_canaries(self.handle, ctypes.byref(n)))
+        return int(n.value)
 
     def synchronize(self):
         self._check(self._L.mfc_synchronize(self.handle))

@@ -54,14 +54,21 @@ def _buffers(slab, torch, device, dtype):
 def exchange_local(slabs, bufs):
     """One halo exchange among slabs held by this process, in flow-axis order: the populations
     leaving slab r upwards go into slab r + 1's low ghost layer and those leaving slab r + 1
-    downwards into slab r's high ghost layer.  bufs[r] = (buffer, buffer) per neighbour pair."""
+    downwards into slab r's high ghost layer.  bufs[r] = (buffer, buffer) per neighbour pair.
+    Each slab works on its own stream, so the packs wait for every slab's step and the unpacks
+    for every pack."""
+    for s in slabs:
+        s.synchronize()
     for r in range(len(slabs) - 1):
-        a, b = slabs[r], slabs[r + 1]
         up, down = bufs[r]
-        a.halo_pack(1, up.data_ptr())
-        b.halo_unpack(0, up.data_ptr())
-        b.halo_pack(0, down.data_ptr())
-        a.halo_unpack(1, down.data_ptr())
+        slabs[r].halo_pack(1, up.data_ptr())
+        slabs[r + 1].halo_pack(0, down.data_ptr())
+    for s in slabs:
+        s.synchronize()
+    for r in range(len(slabs) - 1):
+        up, down = bufs[r]
+        slabs[r + 1].halo_unpack(0, up.data_ptr())
+        slabs[r].halo_unpack(1, down.data_ptr())
 
 
 class LocalSlabs:
