@@ -168,6 +168,10 @@ MFC_API mfc_status mfc_step_flow(mfc_lattice *lat, int nsteps);
 MFC_API mfc_status mfc_step_ade(mfc_lattice *lat, int nsteps);
 /* nsteps fused steps of both lattices; transport uses the same step's flow velocity. */
 MFC_API mfc_status mfc_step_coupled(mfc_lattice *lat, int nsteps);
+/* As mfc_step_coupled, but the stored fields stay those of the last call that stored them (a
+ * check, or a stepping call's last step): for callers that check on their own schedule one step
+ * at a time, such as the slabs of a decomposed lattice between their checks. */
+MFC_API mfc_status mfc_step_coupled_plain(mfc_lattice *lat, int nsteps);
 
 /* Iterate to steady state (Sec. 4: "enough time steps until an equilibrium is reached"),
  * checking the residuals every K steps with CUDA-graph replays of K steps.  Blocks.

@@ -881,6 +881,18 @@ MFC_API mfc_status mfc_step_flow(mfc_lattice *L, int nsteps) { return step_n(L, 
 MFC_API mfc_status mfc_step_ade(mfc_lattice *L, int nsteps) { return step_n(L, KIND_ADE, nsteps); }
 MFC_API mfc_status mfc_step_coupled(mfc_lattice *L, int nsteps) { return step_n(L, KIND_COUPLED, nsteps); }
 
+MFC_API mfc_status mfc_step_coupled_plain(mfc_lattice *L, int nsteps)
+{
+    mfc_status st = enter(L);
+    if (st != MFC_OK) return st;
+    if (nsteps < 0) return fail(L, MFC_ERR_ARG, "nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+        st = enqueue_step(L, KIND_COUPLED, MODE_PLAIN);
+        if (st != MFC_OK) return st;
+    }
+    return MFC_OK;
+}
+
 MFC_API mfc_status mfc_solve_steady(mfc_lattice *L, const mfc_solve_opts *opts, mfc_solve_result *out)
 {
     mfc_status st = enter(L);

@@ -149,6 +149,7 @@ _SIGS = {
     "mfc_step_flow": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mfc_step_ade": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mfc_step_coupled": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mfc_step_coupled_plain": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mfc_solve_steady": (ctypes.c_int, [_vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveResult)]),
     "mfc_biofilm_grow": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_long)]),
@@ -322,6 +323,10 @@ class Lattice:
 
     def step_ade(self, n=1):
         self._check(self._L.mfc_step_ade(self.handle, int(n)))
+
+    def step_coupled_plain(self, n=1):
+        """Fused steps that leave the stored fields as they are (see mfc_step_coupled_plain)."""
+        self._check(self._L.mfc_step_coupled_plain(self.handle, n))
 
     def step_coupled(self, n=1):
         self._check(self._L.mfc_step_coupled(self.handle, int(n)))

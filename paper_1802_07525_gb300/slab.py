@@ -12,7 +12,9 @@ check).  The exchange runs over a ``torch.distributed`` process group (NCCL betw
 CPU), or, for slabs held by one process, as direct device copies (:func:`exchange_local`).
 
 Any object with ``halo_bytes(side)``, ``halo_pack(side, ptr)``, ``halo_unpack(side, ptr)``,
-``step_coupled(n)`` and ``step_check_sums(n)`` can be a slab; :class:`~.mfc.Lattice` is one.
+``step_coupled_plain(n)`` (steps that keep the stored fields, so that a check compares with the
+previous check), ``step_check_sums(n)`` and ``synchronize()`` can be a slab; :class:`~.mfc.Lattice`
+is one.
 """
 from __future__ import annotations
 
@@ -90,7 +92,7 @@ class LocalSlabs:
     def step(self, n: int = 1):
         for _ in range(n):
             for s in self.slabs:
-                s.step_coupled(1)
+                s.step_coupled_plain(1)
             self.exchange()
 
     def check(self, nsteps: int):
@@ -152,7 +154,7 @@ class DistributedSlab:
 
     def step(self, n: int = 1):
         for _ in range(n):
-            self.slab.step_coupled(1)
+            self.slab.step_coupled_plain(1)
             self.exchange()
 
     def check(self, nsteps: int):

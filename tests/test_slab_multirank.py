@@ -44,6 +44,12 @@ class ChainSlab:
         if not self.cut[1]:
             self.f[2, -1] = self.f[2, -2]
 
+    def synchronize(self):
+        pass
+
+    def step_coupled_plain(self, n=1):
+        self.step_coupled(n)
+
     def step_coupled(self, n=1):
         for _ in range(n):
             g = self.f.copy()
