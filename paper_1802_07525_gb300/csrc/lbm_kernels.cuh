@@ -486,11 +486,13 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     const bool at_in = inout && pf == 0 && !a.cut[0];
     const bool at_out = inout && pf == (FA == 0 ? g.nx : g.nz) - 1 && !a.cut[1];
     // How a bounce-back population is fetched.  Unconditional own-opposite loads, selected
-    // afterwards, keep every load independent of the link word (2-D: measured faster in FP32
-    // and FP16); in 3-D (19 + 7 directions under tight register caps) one load per direction from
-    // an address chosen by the link bit halves the load instructions and measured 4% (FP32) and
-    // 3% (FP16) faster.
-    constexpr bool SELECT_LOADS = DIM == 3;
+    // afterwards, keep every load independent of the link word; one load per direction from an
+    // address chosen by the link bit halves the load instructions.  With 64-bit offsets the
+    // selection costs more than it saves in 2-D (measured slower in FP32 and FP16), and pays in
+    // 3-D (19 + 7 directions under tight register caps: 4% faster in FP32, 3% in FP16); with
+    // 32-bit offsets the choice is one 32-bit select, and it pays in 2-D too (2048x1024 FP32
+    // 45.1 -> 43.5 us, 4096x1024 FP16 65.5 -> 61.4 us).
+    constexpr bool SELECT_LOADS = DIM == 3 || sizeof(IX) == 4;
     R u[3] = {R(0), R(0), R(0)};
     // check step: the previous fields of this node (read before this thread overwrites them),
     // issued first so that their latency overlaps the population loads

@@ -518,7 +518,10 @@ bool dev_alloc(mfc_lattice *L, void **p, size_t bytes)
         }
     }
 #ifdef MFC_CHECK_BOUNDS
+    // the guards go on after the zero fill: that ran on the legacy stream (no pool) or on the
+    // lattice stream (pool), so order the lattice stream behind the legacy one first
     char *b = static_cast<char *>(base);
+    if (!L->pool) cudaDeviceSynchronize();
     cudaMemsetAsync(b, GUARD_BYTE, GUARD, L->stream);
     cudaMemsetAsync(b + GUARD + body, GUARD_BYTE, GUARD, L->stream);
     if (!L->pool) cudaStreamSynchronize(L->stream);

@@ -2,8 +2,8 @@
 
 Slabs held by one process on one GPU, exchanging halos through device buffers after every step,
 compute exactly what the whole lattice computes: the same kernels on the same values.  Checked on
-the populations after many steps (bit for bit in FP32), on the summed check sums, and on a
-steady solve.
+the populations after many steps (bit for bit in FP32), on the summed check sums (to the FP32
+rounding of their per-block partials, whose node ranges differ), and on a steady solve.
 """
 import numpy as np
 import pytest
@@ -74,10 +74,11 @@ def test_slabs_compute_what_the_whole_lattice_computes(P, name, bc, nslab):
         for which in (P.MFC_POP_FLOW, P.MFC_POP_ADE):
             a, b = joined(P, w, slabs, which), whole.read_populations(which)
             assert np.array_equal(a, b), (target, which, float(np.abs(a - b).max()))
-    # a check step: the sums over the slabs are the whole lattice's sums
+    # a check step: the sums over the slabs are the whole lattice's sums, to the FP32 rounding of
+    # the per-block partial sums (the slabs' blocks cover other node ranges)
     s_local = local.check(20)
     s_whole = whole.step_check_sums(20)
-    assert np.allclose(s_local, s_whole, rtol=1e-11, atol=1e-300)
+    assert np.allclose(s_local, s_whole, rtol=1e-6, atol=1e-300)
     for g in slabs + [whole]:
         g.close()
 
@@ -92,8 +93,9 @@ def test_slab_steady_solve_matches_the_whole_lattice(P):
                             max_steps=w.max_steps, check_every=100)
     assert r["status"] == "converged" and rw.status == P.MFC_OK
     assert r["steps"] == rw.steps_flow
-    assert r["current"] == pytest.approx(rw.current, rel=1e-12)
-    assert r["res_flow"] == pytest.approx(rw.res_flow, rel=1e-9)
+    # the sums agree to the FP32 rounding of the per-block partials
+    assert r["current"] == pytest.approx(rw.current, rel=1e-6)
+    assert r["res_flow"] == pytest.approx(rw.res_flow, rel=1e-4)
     assert np.array_equal(joined(P, w, slabs, P.MFC_POP_ADE), whole.read_populations(P.MFC_POP_ADE))
     assert S.residuals(r["sums"], 100)[0] == pytest.approx(r["res_flow"])
     for g in slabs + [whole]:
