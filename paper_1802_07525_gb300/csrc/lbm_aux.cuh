@@ -100,18 +100,18 @@ __device__ __forceinline__ bool mask_blocked(const MaskArgs &m, int x, int y, in
 }
 
 // Link words from the node classes; (re)initialise populations and fields of nodes whose class
-// changed (or of every node when resetting); count the open nodes.
+// changed (or of every node when resetting); count the open nodes.  One thread per node on a
+// (row / block, ny, nz) grid, so that no index needs a division (64-bit divisions per node made
+// this kernel take milliseconds on a lattice of millions of nodes).
 template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kernel(const MaskArgs m)
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM, AQ>;
     using LK = Links<DIM, AQ>;
     using LinkT = typename LK::T;
-    const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
-         q += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        node_xyz(m.geo, q, &x, &y, &z);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x < m.geo.nx) {
+        const long long q = x + (long long)m.geo.nx * (y + (long long)m.geo.ny * z);
         const long long k = m.geo.at(x, y, z);
         const uint8_t c = m.cls_new[q];
         uint32_t L = 0;
@@ -147,8 +147,7 @@ template <int DIM, int AQ = default_aq<DIM>()> __global__ void build_links_kerne
             for (int ax = 0; ax < DIM; ++ax) store_field(m.fld_u, m.dbl, ax * m.geo.plane + k, 0.0);
         }
         if (m.reset || !a_open) store_field(m.fld_c, m.dbl, k, -(double)m.c_ref);
-        // open-node counts: one atomic per warp (one per node serialises on the two counters,
-        // milliseconds on a lattice of millions of nodes)
+        // open-node counts: one atomic per warp on each of the two counters
         const unsigned act = __activemask();
         const unsigned fo = __ballot_sync(act, f_open), ao = __ballot_sync(act, a_open);
         if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {

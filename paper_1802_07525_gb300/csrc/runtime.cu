@@ -25,11 +25,10 @@ namespace mfc {
 
 cudaError_t launch_links(int dim, int aq, const MaskArgs &m, cudaStream_t s)
 {
-    const long long N = (long long)m.geo.nx * m.geo.ny * m.geo.nz;
-    const int blocks = (int)((N + 255) / 256 < 65535 * 8 ? (N + 255) / 256 : 65535 * 8);
-    if (dim == 2 && aq == 9) build_links_kernel<2, 9><<<blocks, 256, 0, s>>>(m);
-    else if (dim == 2) build_links_kernel<2><<<blocks, 256, 0, s>>>(m);
-    else build_links_kernel<3><<<blocks, 256, 0, s>>>(m);
+    const dim3 grid((unsigned)((m.geo.nx + 255) / 256), (unsigned)m.geo.ny, (unsigned)m.geo.nz);
+    if (dim == 2 && aq == 9) build_links_kernel<2, 9><<<grid, 256, 0, s>>>(m);
+    else if (dim == 2) build_links_kernel<2><<<grid, 256, 0, s>>>(m);
+    else build_links_kernel<3><<<grid, 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
