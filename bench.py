@@ -623,7 +623,7 @@ def serve_phase(P, reqs, works, rate_scale):
             time.sleep(delay)
         tickets.append(b.submit(w.shape, w.cls, tol_flow=w.tol, tol_ade=w.tol,
                                 max_steps=w.max_steps, **wkw(w)))
-    res = [b.wait(t, timeout_s=600.0) for t in tickets]
+    res = [b.wait(t, timeout_s=3600.0) for t in tickets]
     b.stop()
     st = b.stats()
     b.close()
@@ -632,6 +632,7 @@ def serve_phase(P, reqs, works, rate_scale):
 
     lat = sorted(x["t_done"] - x["t_submit"] for x in res)
     conv = sorted(x["t_done"] - x["t_submit"] for x in res if x["status"] == P.MFC_OK)
+    sc = sorted(x["steps_flow"] for x in res if x["status"] == P.MFC_OK)
     span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
     first, last = min(x["t_submit"] for x in res), max(x["t_submit"] for x in res)
     return {"requests": len(res), "solves_per_s": len(res) / span, "span_s": span,
@@ -643,13 +644,17 @@ def serve_phase(P, reqs, works, rate_scale):
             "p50_converged_s": pct(conv, 0.5), "p99_converged_s": pct(conv, 0.99),
             "p50_all_s": pct(lat, 0.5), "p99_all_s": pct(lat, 0.99), "max_s": lat[-1],
             "mean_steps": statistics.mean(x["steps_flow"] for x in res),
+            "steps_converged_p50_p99_max": ([pct(sc, 0.5), pct(sc, 0.99), sc[-1]] if sc else None),
+            # the requests that did not converge: shape and steps
+            "not_converged": [[list(w.shape), x["steps_flow"], x["status"]]
+                              for w, x in zip(works, res) if x["status"] != P.MFC_OK],
             "check_every": st["check_every"], "block": st["block"],
             "peak_bytes": st["bytes_peak"]}
 
 
 def leg_serve(P, count):
     """Serving: Poisson arrivals of 2-D (512..2048 x 256..1024) and 3-D (64^3..192x96x96)
-    steady-solve requests (tol 1e-7, cap 3e5 steps), 150 GB admission budget.  Phase 1 offers
+    steady-solve requests (tol 1e-7, cap 1e6 steps), 150 GB admission budget.  Phase 1 offers
     the stream at 200/s (capacity); phase 2 offers a second stream at 0.8x that capacity.
     Latencies are time to converged solution (submission to result, converged requests), with
     the requests that ended otherwise counted beside them."""

@@ -485,7 +485,9 @@ MFC_API mfc_status mfc_batch_destroy(mfc_batch *batch);
  * be MFC_CONCURRENT, check_every is ignored (the batch's K applies).  rho, u, c: optional host
  * buffers (N, dim*N, N doubles, as mfc_read_fields fills them) that the batch fills when the
  * solve ends; they must stay valid until then.  *ticket identifies the request.  Fails with
- * MFC_ERR_ARG for a bad request and MFC_ERR_OOM_BUDGET when it can never fit the budget. */
+ * MFC_ERR_ARG for a bad request (including a lattice whose largest population array, the larger
+ * set's Q times the pitched plane, reaches 2^31 elements: the batch kernel's offsets are 32-bit)
+ * and MFC_ERR_OOM_BUDGET when it can never fit the budget. */
 MFC_API mfc_status mfc_batch_submit(mfc_batch *batch, const mfc_lattice_desc *desc,
                                     const mfc_params *params, const uint8_t *node_class,
                                     const mfc_solve_opts *opts, double *rho, double *u, double *c,

@@ -842,6 +842,7 @@ MFC_API mfc_status mfc_batch_submit(mfc_batch *B, const mfc_lattice_desc *desc, 
     if (d.precision != B->opts.precision) return MFC_ERR_ARG;
     if (d.ade_q == 9) return MFC_ERR_ARG;  // batches run the default transport sets
     if (d.cut[0] || d.cut[1]) return MFC_ERR_ARG;  // whole lattices only
+    if (lattice_max_elements(&d) >= (1ll << 31)) return MFC_ERR_ARG;  // 32-bit element offsets
     if (opts->mode != MFC_CONCURRENT || opts->max_steps < 0 || !(opts->tol_flow >= 0.0) ||
         !(opts->tol_ade >= 0.0))
         return MFC_ERR_ARG;

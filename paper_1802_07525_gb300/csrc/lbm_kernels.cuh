@@ -722,9 +722,10 @@ template <int DIM, typename ST> struct BatchArgs {
     int parity;
 };
 
-// The tile loop and the shared argument block take registers of their own: 2-D batch steps are
-// capped at 48 registers (5 blocks of 256 threads per SM), where they do not spill; 3-D batch
-// steps take the caps of the 3-D step kernel.
+// Element offsets are 32-bit: a batch admits only instances whose population arrays have fewer
+// than 2^31 elements.  The tile loop and the shared argument block take registers of their own:
+// 2-D batch steps are capped at 48 registers (5 blocks of 256 threads per SM), where they do not
+// spill; 3-D batch steps take the caps of the 3-D step kernel.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE>
 __global__ void __launch_bounds__(256, DIM == 2 ? 5 : StepOccupancy<DIM, MODE, ST>::blocks)
     lbm_batch_kernel(const BatchArgs<DIM, ST> b)
@@ -747,10 +748,11 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 5 : StepOccupancy<DIM, MODE, S
         ArithT<ST> acc[NSUM];
 #pragma unroll
         for (int m = 0; m < NSUM; ++m) acc[m] = 0;
+        constexpr int AQ = default_aq<DIM>();
         if (tile_on_open_boundary<DIM>(sa.geo, sa.bc, tile.x0, blockDim.x, tile.y, tile.z))
-            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY>(sa, tile.x0, tile.y, tile.z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_BOUNDARY, AQ, SINK_RUNTIME, int>(sa, tile.x0, tile.y, tile.z, acc);
         else
-            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR>(sa, tile.x0, tile.y, tile.z, acc);
+            step_node<DIM, ST, FLOW, ADE, MODE, B_INTERIOR, AQ, SINK_RUNTIME, int>(sa, tile.x0, tile.y, tile.z, acc);
         if (MODE == MODE_CHECK) {
             block_partials(acc, b.partials + (size_t)t * NSUM);
             __syncthreads();  // the reduction's shared memory is reused by the next tile

@@ -251,6 +251,12 @@ int max_launch_blocks(const Layout &l)
 
 }  // namespace
 
+long long mfc::lattice_max_elements(const mfc_lattice_desc *d)
+{
+    const Layout l = layout_of(d);
+    return (long long)(l.qf > l.qa ? l.qf : l.qa) * l.geo.plane;
+}
+
 void mfc::fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h)
 {
     memset(h, 0, sizeof *h);

@@ -82,6 +82,9 @@ mfc_status lattice_create(const mfc_lattice_desc *desc, const mfc_params *params
                           mfc_lattice **out, std::string *why);
 // The checks mfc_create_lattice applies to a descriptor and parameters.
 mfc_status validate_lattice(const mfc_lattice_desc *desc, const mfc_params *params, std::string *why);
+// Elements of the largest population array of a lattice of this descriptor (the larger set's Q
+// times the pitched plane): the batch kernel addresses them with 32-bit offsets.
+long long lattice_max_elements(const mfc_lattice_desc *desc);
 // Step arguments of the lattice for one step of `kind` in `mode` from its current buffers.
 void fill_step(const mfc_lattice *L, int kind, int mode, StepHost *h);
 // Seconds on the steady clock (the clock of mfc_clock and of the batch time stamps).

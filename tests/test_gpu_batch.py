@@ -170,6 +170,10 @@ def test_bad_requests_are_refused(P):
     with pytest.raises(P.MfcError) as e:  # tau <= 1/2
         b.submit(w.shape, w.cls, tau=0.5)
     assert e.value.status == P.MFC_ERR_ARG
+    with pytest.raises(P.MfcError) as e:  # population arrays past 32-bit element offsets
+        shape = (512, 512, 430)  # 19 x the pitched plane > 2^31 elements; no fields requested
+        b.submit(shape, np.zeros(shape, np.uint8), fields=False, u_in=0.01)
+    assert e.value.status == P.MFC_ERR_ARG
     bad = w.cls.copy()
     bad[5] = 9
     with pytest.raises(P.MfcError):
