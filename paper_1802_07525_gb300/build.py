@@ -29,7 +29,7 @@ OBJ_DIR_CHECK = os.path.join(HERE, "_build_check")
 SOURCES = ["lbm2d_f32.cu", "lbm2d_f16.cu", "lbm3d_f32.cu", "lbm3d_f16.cu", "lbm2d9_f32.cu",
            "lbm2d9_f16.cu", "lbm2d_f64.cu", "lbm3d_f64.cu", "lbm2d9_f64.cu", "runtime.cu", "batch.cu",
            "noalloc.cu", "electro.cu", "agent.cu", "slab.cu"]
-HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh", "lbm_aux.cuh", "lbm_launch.cuh", "mfc_internal.h",
+HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_aux.cuh", "lbm_launch.cuh", "mfc_internal.h",
            "runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -67,7 +67,7 @@ def _digest(verbose: bool, check_bounds: bool = False) -> str:
 
 
 # The files each step-kernel translation unit compiles from (the TU and the headers it includes).
-KERNEL_TU_FILES = ["lbm_launch.cuh", "mfc_internal.h", "lbm_kernels.cuh", "lbm_lattice.cuh"]
+KERNEL_TU_FILES = ["lbm_launch.cuh", "mfc_internal.h", "lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_pair.cuh"]
 
 
 def kernel_digest(tu: str) -> str:

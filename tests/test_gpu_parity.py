@@ -402,6 +402,60 @@ def test_launch_variants_agree(P, shape, bc, prec):
         assert np.allclose(out[3], ref[3], rtol=1e-3 if prec else 1e-5, atol=1e-12), v
 
 
+@pytest.mark.parametrize("shape,bc,k_half", [
+    ((300, 37), (2, 0), 0.0),       # inlet/outlet, walls; odd ny: the last pair has one row
+    ((133, 20), (2, 1), 0.0),       # periodic cross axis
+    ((64, 24), (1, 1), 0.0),        # fully periodic
+    ((45, 9), (0, 0), 0.05),        # closed box, saturating consumption
+    ((23, 11, 17), (0, 0, 2), 0.0),  # 3-D inlet/outlet along z, odd ny
+    ((16, 9, 10), (1, 1, 1), 0.05),
+])
+def test_paired_plain_steps_agree_with_single_node_steps(P, shape, bc, k_half):
+    """FP16 storage: plain coupled steps of two rows per thread (paired FP32 arithmetic, 32-bit
+    offsets) against single-node plain steps (64-bit offsets) from the same state.  The two group
+    the FP32 operations differently, so a stored FP16 value may round to the neighbouring one:
+    after one step every population agrees within two FP16 spacings of the largest, after 50
+    steps within the FP16 bound of the launch-variant test."""
+    dim = len(shape)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(N + 7)
+    r = rng.random(N)
+    cls = np.where(r < 0.15, 3, np.where(r < 0.3, 4, np.where(r < 0.35, 5, 0))).astype(np.uint8)
+    kw = dict(tau=0.7, tau_c=0.9, u_in=0.03, c_in=0.8, k_sink=0.01, k_half=k_half)
+    f0 = g0 = None
+    if bc[0] != 2 and (dim == 2 or bc[2] != 2):
+        o = oracle.Oracle(shape, cls, bc=bc, **{k: v for k, v in kw.items() if k != "k_half"})
+        for k in np.nonzero((cls & 1) == 0)[0]:
+            o.f[:, k] = oracle.flow_equilibrium(dim, 1.0 + 0.01 * rng.standard_normal(),
+                                                0.02 * rng.standard_normal(dim))
+        f0 = o.f.copy()
+        g0 = np.where((cls & 2) == 0, rng.random((o.qa, N)) * 0.2, 0.0)
+    lats = []
+    for off32 in (1, 0):
+        g = P.Lattice(shape, bc=bc, precision=P.MFC_FP16_DEV, **kw)
+        g.set_geometry(cls)
+        g.set_launch(block=128, offsets32=off32)
+        if f0 is not None:
+            g.write_populations(P.MFC_POP_FLOW, f0)
+            g.write_populations(P.MFC_POP_ADE, g0)
+        else:
+            g.step_coupled(20)  # a developed, non-uniform state from the inlet
+        lats.append(g)
+    a, b = lats
+    # the same starting state in both (the warm-up steps above may differ by FP16 roundings)
+    for which in (P.MFC_POP_FLOW, P.MFC_POP_ADE):
+        b.write_populations(which, a.read_populations(which))
+    for n, rel in ((1, 2.0 ** -10), (49, None)):
+        a.step_coupled_plain(n)
+        b.step_coupled_plain(n)
+        for which in (P.MFC_POP_FLOW, P.MFC_POP_ADE):
+            pa, pb = a.read_populations(which), b.read_populations(which)
+            tol = rel * np.abs(pb).max() + 1e-7 if rel else 2e-3
+            assert maxabs(pa, pb) <= tol, (n, which, maxabs(pa, pb), tol)
+    for g in lats:
+        g.close()
+
+
 # ------------------------------------------------------------------------------------------
 # Paper-literal transport: D2Q9 with the equilibrium of Eq. 5 (C in place of rho)
 # ------------------------------------------------------------------------------------------
