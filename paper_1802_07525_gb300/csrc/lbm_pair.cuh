@@ -85,13 +85,27 @@ template <int DIM, typename ST> struct PairedStep {
 // Resident blocks of 256 threads per SM: 3-D pairs hold 2 x 19 flow populations at once, 2-D
 // pairs 2 x 9.
 template <int DIM, typename ST> struct PairOccupancy {
-    static constexpr int blocks = DIM == 3 ? 3 : 5;
+    static constexpr int blocks = DIM == 3 ? 3 : 4;
 };
 
+// The link words of nodes (x, y, z) and (x, y + 1, z) (the second repeats the first where y + 1 =
+// ny), and the element offset of the first.
+template <int DIM, typename ST>
+__device__ __forceinline__ int pair_links(const StepArgs<DIM, ST> &a, int x, int y, int z, uint32_t (&L)[2])
+{
+    const Geo &g = a.geo;
+    const int k0 = (int)g.row0 + z * (int)g.zs + y * g.px + x;
+    const int k1 = y + 1 < g.ny ? k0 + g.px : k0;
+    L[0] = __ldg(a.link + MFC_IDX(k0, g.plane));
+    L[1] = __ldg(a.link + MFC_IDX(k1, g.plane));
+    return k0;
+}
+
 // One plain coupled step of nodes (x0 + threadIdx.x, y + l, z), l = 0, 1 (lane 1 absent where
-// y + 1 = ny), with 32-bit element offsets and the default transport set.  BFORM as in step_node.
+// y + 1 = ny; x < nx), given their link words, with 32-bit element offsets and the default
+// transport set.  BFORM as in step_node.
 template <int DIM, typename ST, int BFORM, int SINK>
-__device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, int y, int z)
+__device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, int y, int z, const uint32_t (&L)[2])
 {
     using F = FlowSet<DIM>;
     using A = AdeSet<DIM>;
@@ -100,12 +114,10 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
     static_assert(!A::quadratic, "linear transport equilibrium");
     const Geo g = a.geo;
     const int x = x0 + threadIdx.x;
-    if (x >= g.nx) return;
     const bool has1 = y + 1 < g.ny;
     const int P = (int)g.plane;
     const int k0 = (int)g.row0 + z * (int)g.zs + y * g.px + x;
     const int k[2] = {k0, has1 ? k0 + g.px : k0};
-    const uint32_t L[2] = {__ldg(a.link + MFC_IDX(k[0], P)), __ldg(a.link + MFC_IDX(k[1], P))};
     constexpr bool READER = BFORM != B_WRITER;
     const int y1 = has1 ? y + 1 : y;
     const bool bnd_tile = BFORM == B_WRITER ? (tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z) ||
@@ -253,23 +265,47 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
     }
 }
 
-// Plain coupled step, two rows per thread: grid (row / block, ceil(ny / 2), nz).
+// Row pairs per thread: a thread steps PairRows pairs of rows one after the other, and loads the
+// link words of the next pair before it steps the current one, so that the link loads do not
+// stand between the population loads of consecutive pairs and their wait.
+template <int DIM, typename ST> struct PairRows {
+    static constexpr int value = 4;
+};
+
+// Plain coupled step, two rows per thread at a time: grid (row / block, ceil(ceil(ny / 2) / R),
+// nz) with R = PairRows.
 template <int DIM, typename ST, int SINK>
 __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_kernel(const StepArgs<DIM, ST> a)
 {
+    constexpr int R = PairRows<DIM, ST>::value;
     const int x0 = blockIdx.x * blockDim.x;
-    const int y = 2 * (int)blockIdx.y;
+    const int x = x0 + (int)threadIdx.x;
+    if (x >= a.geo.nx) return;
+    const int npairs = (a.geo.ny + 1) / 2;
+    const int p0 = (int)blockIdx.y * R;
     // 3-D: the last plane first, as in lbm_step_kernel
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
-    if constexpr (ReaderBoundaries<DIM, ST>::step) {
-        const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
-        if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
-            tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
-            step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z);
-        else
-            step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z);
-    } else {
-        step_pair<DIM, ST, B_WRITER, SINK>(a, x0, y, z);
+    uint32_t L[2];
+    pair_links(a, x, 2 * p0, z, L);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int p = p0 + r;
+        if (p >= npairs) break;
+        const int y = 2 * p;
+        uint32_t Ln[2] = {0u, 0u};
+        if (r + 1 < R && p + 1 < npairs) pair_links(a, x, y + 2, z, Ln);
+        if constexpr (ReaderBoundaries<DIM, ST>::step) {
+            const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
+            if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
+                tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
+                step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z, L);
+            else
+                step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z, L);
+        } else {
+            step_pair<DIM, ST, B_WRITER, SINK>(a, x0, y, z, L);
+        }
+        L[0] = Ln[0];
+        L[1] = Ln[1];
     }
 }
 
