@@ -42,6 +42,14 @@ cudaError_t launch_sink(const Args &a, const StepHost &h, cudaStream_t s)
                 break;
             }
         }
+        if constexpr (StepRows<D, ST>::value > 1) {
+            if (h.idx32) {
+                constexpr int R = StepRows<D, ST>::value;
+                const dim3 rows((unsigned)h.grid, (unsigned)((h.geo.ny + R - 1) / R), (unsigned)h.geo.nz);
+                lbm_rows_kernel<D, ST, FLOW, ADE, AQ, SINK><<<rows, h.block, 0, s>>>(a);
+                break;
+            }
+        }
         if (h.idx32) lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK, true><<<grid, h.block, 0, s>>>(a);
         else lbm_step_kernel<D, ST, FLOW, ADE, MODE_PLAIN, AQ, SINK><<<grid, h.block, 0, s>>>(a);
         break;

@@ -266,14 +266,16 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
 }
 
 // Row pairs per thread: a thread steps PairRows pairs of rows one after the other, and loads the
-// link words of the next pair before it steps the current one, so that the link loads do not
-// stand between the population loads of consecutive pairs and their wait.
+// link words of its next pair before it steps the current one, so that the link loads do not
+// stand between the population loads of consecutive pairs and their wait.  Iteration r of block
+// row b takes pair b + r G (G = gridDim.y), so that the blocks resident at one time sweep one
+// band of rows, as with one pair per thread.
 template <int DIM, typename ST> struct PairRows {
-    static constexpr int value = 4;
+    static constexpr int value = 2;
 };
 
-// Plain coupled step, two rows per thread at a time: grid (row / block, ceil(ceil(ny / 2) / R),
-// nz) with R = PairRows.
+// Plain coupled step, two rows per thread at a time: grid (row / block, G = ceil(ceil(ny / 2) /
+// R), nz) with R = PairRows.
 template <int DIM, typename ST, int SINK>
 __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_kernel(const StepArgs<DIM, ST> a)
 {
@@ -282,18 +284,18 @@ __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_
     const int x = x0 + (int)threadIdx.x;
     if (x >= a.geo.nx) return;
     const int npairs = (a.geo.ny + 1) / 2;
-    const int p0 = (int)blockIdx.y * R;
+    const int p0 = (int)blockIdx.y, G = (int)gridDim.y;
     // 3-D: the last plane first, as in lbm_step_kernel
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     uint32_t L[2];
     pair_links(a, x, 2 * p0, z, L);
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
-        const int p = p0 + r;
+        const int p = p0 + r * G;
         if (p >= npairs) break;
         const int y = 2 * p;
         uint32_t Ln[2] = {0u, 0u};
-        if (r + 1 < R && p + 1 < npairs) pair_links(a, x, y + 2, z, Ln);
+        if (r + 1 < R && p + G < npairs) pair_links(a, x, y + 2 * G, z, Ln);
         if constexpr (ReaderBoundaries<DIM, ST>::step) {
             const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
             if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
