@@ -847,7 +847,9 @@ def main():
     bytes_per_launch = step_bytes(w.dim, sb, flow_open, ade_open)
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
-    kname = "lbm_step_kernel<%d,%s,true,true,0>" % (w.dim, "half" if sb == 2 else "float")
+    # FP16 storage steps two rows per thread with paired FP32 arithmetic (lbm_pair_kernel)
+    kname = ("lbm_pair_kernel<%d,half,0>" % w.dim if sb == 2 else
+             "lbm_step_kernel<%d,float,true,true,0>" % w.dim)
     traffic = traffic_record(kname)
 
     # end to end through the public API with host buffers: upload classes from pinned memory,

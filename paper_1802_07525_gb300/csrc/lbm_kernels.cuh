@@ -456,11 +456,9 @@ enum : int { SINK_LINEAR = 0, SINK_MONOD = 1, SINK_RUNTIME = 2 };
 
 // IX: the integer type of the element offsets: long long, or int where every population array
 // has fewer than 2^31 elements (one IMAD.WIDE per address instead of 64-bit offset arithmetic).
-// LPRE: the caller loaded the node's link word (Lpre) ahead of the step.
 template <int DIM, typename ST, bool FLOW, bool ADE, int MODE, int BFORM, int AQ, int SINK = SINK_RUNTIME,
-          typename IX = long long, bool LPRE = false>
-__device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, ArithT<ST> (&acc)[NSUM],
-                                          uint32_t Lpre = 0)
+          typename IX = long long>
+__device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0, int y, int z, ArithT<ST> (&acc)[NSUM])
 {
     using R = ArithT<ST>;
     static_assert(BFORM == B_WRITER || AdeSet<DIM, AQ>::Q == default_aq<DIM>(),
@@ -474,7 +472,7 @@ __device__ __forceinline__ void step_node(const StepArgs<DIM, ST, AQ> &a, int x0
     const bool valid = MODE != MODE_CHECK || x < g.nx;
     const IX k = (IX)g.row0 + (IX)z * (IX)g.zs + (IX)y * (IX)g.px + (IX)(x < g.nx ? x : g.nx - 1);
     const IX P = (IX)g.plane;
-    const uint32_t L = LPRE ? Lpre : (uint32_t)__ldg(a.link + MFC_IDX(k, P));
+    const uint32_t L = __ldg(a.link + MFC_IDX(k, P));
     constexpr bool READER = BFORM != B_WRITER;
     const bool bnd_tile = BFORM == B_WRITER ? tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z)
                                             : BFORM == B_BOUNDARY;
@@ -704,57 +702,6 @@ __global__ void __launch_bounds__(256, StepOccupancy<DIM, MODE, ST, AQ, IDX32>::
     if (MODE == MODE_CHECK)
         block_partials(acc, a.partials + ((size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y *
                                                                                   blockIdx.z)) * NSUM);
-}
-
-// Rows per thread of the plain single-node step (1: lbm_step_kernel, one node per thread), and
-// the resident blocks of 256 threads per SM of the row loop (the loop state takes registers: the
-// 2-D FP32 step gets 40).
-template <int DIM, typename ST> struct StepRows {
-    static constexpr int value = 1;
-};
-template <int DIM, typename ST, int AQ> struct RowsOccupancy {
-    static constexpr int blocks = (DIM == 2 && sizeof(ST) == 4) ? 6 : StepOccupancy<DIM, MODE_PLAIN, ST, AQ, true>::blocks;
-};
-
-// Plain step, StepRows rows per thread: a thread steps node x of rows b, b + G, .. b + (R - 1) G
-// (b = blockIdx.y, G = gridDim.y = ceil(ny / R)) in turn and loads the next row's link word
-// before it steps the current one; the blocks resident at one time sweep one band of rows.  Grid
-// (row / block, G, nz); 32-bit element offsets.
-template <int DIM, typename ST, bool FLOW, bool ADE, int AQ, int SINK>
-__global__ void __launch_bounds__(256, RowsOccupancy<DIM, ST, AQ>::blocks) lbm_rows_kernel(const StepArgs<DIM, ST, AQ> a)
-{
-    constexpr int R = StepRows<DIM, ST>::value;
-    using LT = typename StepArgs<DIM, ST, AQ>::LinkT;
-    const Geo &g = a.geo;
-    const int x0 = blockIdx.x * blockDim.x;
-    const int x = x0 + (int)threadIdx.x;
-    if (x >= g.nx) return;
-    const int y0 = (int)blockIdx.y, G = (int)gridDim.y;
-    const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
-    int k = (int)g.row0 + z * (int)g.zs + y0 * g.px + x;
-    const int kstep = G * g.px;
-    const LT *link = a.link;
-    uint32_t L = __ldg(link + MFC_IDX(k, g.plane));
-    ArithT<ST> acc[NSUM];  // plain steps add nothing
-#pragma unroll
-    for (int m = 0; m < NSUM; ++m) acc[m] = ArithT<ST>(0);
-#pragma unroll 1
-    for (int r = 0; r < R; ++r) {
-        const int y = y0 + r * G;
-        if (y >= g.ny) break;
-        uint32_t Ln = 0u;
-        if (r + 1 < R && y + G < g.ny) Ln = __ldg(link + MFC_IDX(k + kstep, g.plane));
-        if constexpr (ReaderBoundaries<DIM, ST, AQ>::step) {
-            if (tile_on_open_boundary<DIM>(g, a.bc, x0, blockDim.x, y, z))
-                step_node<DIM, ST, FLOW, ADE, MODE_PLAIN, B_BOUNDARY, AQ, SINK, int, true>(a, x0, y, z, acc, L);
-            else
-                step_node<DIM, ST, FLOW, ADE, MODE_PLAIN, B_INTERIOR, AQ, SINK, int, true>(a, x0, y, z, acc, L);
-        } else {
-            step_node<DIM, ST, FLOW, ADE, MODE_PLAIN, B_WRITER, AQ, SINK, int, true>(a, x0, y, z, acc, L);
-        }
-        L = Ln;
-        k += kstep;
-    }
 }
 
 // ---- many lattices in one launch -------------------------------------------------------------

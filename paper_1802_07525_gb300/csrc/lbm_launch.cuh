@@ -35,18 +35,8 @@ cudaError_t launch_sink(const Args &a, const StepHost &h, cudaStream_t s)
         // coupled steps two rows per thread where that was measured faster
         if constexpr (FLOW && ADE && AQ == default_aq<D>() && PairedStep<D, ST>::value) {
             if (h.idx32) {
-                constexpr int R = PairRows<D, ST>::value;
-                const int npairs = (h.geo.ny + 1) / 2;
-                const dim3 pairs((unsigned)h.grid, (unsigned)((npairs + R - 1) / R), (unsigned)h.geo.nz);
+                const dim3 pairs((unsigned)h.grid, (unsigned)((h.geo.ny + 1) / 2), (unsigned)h.geo.nz);
                 lbm_pair_kernel<D, ST, SINK><<<pairs, h.block, 0, s>>>(a);
-                break;
-            }
-        }
-        if constexpr (StepRows<D, ST>::value > 1) {
-            if (h.idx32) {
-                constexpr int R = StepRows<D, ST>::value;
-                const dim3 rows((unsigned)h.grid, (unsigned)((h.geo.ny + R - 1) / R), (unsigned)h.geo.nz);
-                lbm_rows_kernel<D, ST, FLOW, ADE, AQ, SINK><<<rows, h.block, 0, s>>>(a);
                 break;
             }
         }

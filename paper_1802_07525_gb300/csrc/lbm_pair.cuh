@@ -82,10 +82,12 @@ template <int DIM, typename ST> struct PairedStep {
     static constexpr bool value = std::is_same<ST, __half>::value;
 };
 
-// Resident blocks of 256 threads per SM: 3-D pairs hold 2 x 19 flow populations at once, 2-D
-// pairs 2 x 9.
+// Resident blocks of 256 threads per SM: 3-D pairs hold 2 x 19 flow populations at once (80
+// registers), 2-D pairs 2 x 9 (48).  Measured on the 256x128x128 electrode and the 4096x1024
+// anode: 3-D 117.5 us at 3 blocks against 121.1 at 4 and 141.8 at 2; 2-D 58.7 us at 5 blocks
+// against 62.6 at 4.
 template <int DIM, typename ST> struct PairOccupancy {
-    static constexpr int blocks = DIM == 3 ? 3 : 4;
+    static constexpr int blocks = DIM == 3 ? 3 : 5;
 };
 
 // The link words of nodes (x, y, z) and (x, y + 1, z) (the second repeats the first where y + 1 =
@@ -265,49 +267,29 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
     }
 }
 
-// Row pairs per thread: a thread steps PairRows pairs of rows one after the other, and loads the
-// link words of its next pair before it steps the current one, so that the link loads do not
-// stand between the population loads of consecutive pairs and their wait.  Iteration r of block
-// row b takes pair b + r G (G = gridDim.y), so that the blocks resident at one time sweep one
-// band of rows, as with one pair per thread.
-template <int DIM, typename ST> struct PairRows {
-    static constexpr int value = 2;
-};
-
-// Plain coupled step, two rows per thread at a time: grid (row / block, G = ceil(ceil(ny / 2) /
-// R), nz) with R = PairRows.
+// Plain coupled step, two rows per thread: grid (row / block, ceil(ny / 2), nz).  (A loop over
+// several row pairs per thread, loading the next pair's link words ahead, measured slower at
+// every depth tried.)
 template <int DIM, typename ST, int SINK>
 __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_kernel(const StepArgs<DIM, ST> a)
 {
-    constexpr int R = PairRows<DIM, ST>::value;
     const int x0 = blockIdx.x * blockDim.x;
     const int x = x0 + (int)threadIdx.x;
     if (x >= a.geo.nx) return;
-    const int npairs = (a.geo.ny + 1) / 2;
-    const int p0 = (int)blockIdx.y, G = (int)gridDim.y;
+    const int y = 2 * (int)blockIdx.y;
     // 3-D: the last plane first, as in lbm_step_kernel
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     uint32_t L[2];
-    pair_links(a, x, 2 * p0, z, L);
-#pragma unroll 1
-    for (int r = 0; r < R; ++r) {
-        const int p = p0 + r * G;
-        if (p >= npairs) break;
-        const int y = 2 * p;
-        uint32_t Ln[2] = {0u, 0u};
-        if (r + 1 < R && p + G < npairs) pair_links(a, x, y + 2 * G, z, Ln);
-        if constexpr (ReaderBoundaries<DIM, ST>::step) {
-            const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
-            if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
-                tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
-                step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z, L);
-            else
-                step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z, L);
-        } else {
-            step_pair<DIM, ST, B_WRITER, SINK>(a, x0, y, z, L);
-        }
-        L[0] = Ln[0];
-        L[1] = Ln[1];
+    pair_links(a, x, y, z, L);
+    if constexpr (ReaderBoundaries<DIM, ST>::step) {
+        const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
+        if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
+            tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
+            step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z, L);
+        else
+            step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z, L);
+    } else {
+        step_pair<DIM, ST, B_WRITER, SINK>(a, x0, y, z, L);
     }
 }
 
