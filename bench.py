@@ -440,16 +440,26 @@ def traffic_record(kernel):
 # ---- GPU legs --------------------------------------------------------------------------------
 
 def time_plain_steps(P, lat, stream, M=400):
-    """Average duration of the plain fused step kernel: M launches on the lattice stream,
-    bracketed by CUDA events on that stream."""
+    """Average duration of the plain fused step kernel, in ms, two ways, each bracketed by CUDA
+    events on the lattice stream: (1) launched as mfc_solve_steady launches it, one CUDA graph of
+    M steps (M - 2 plain steps, one that stores the fields, one check step), the block's time over
+    M: an upper bound on the plain launch's duration, since the other two steps take longer;
+    (2) M direct launches (mfc_step_coupled), which adds each launch's gap."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solve = dict(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=M, check_every=M)
+    lat.solve_steady(**solve)  # captures the graph
+    e0.record(stream)
+    lat.solve_steady(**solve)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / M
     lat.step_coupled(20)
     e0.record(stream)
     lat.step_coupled(M)
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / M
+    return graph_ms, e0.elapsed_time(e1) / M
 
 
 def step_bytes(dim, prec_bytes, flow_open, ade_open, ade_q=0):
@@ -493,16 +503,17 @@ def leg_variants(P, peak):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        kern_ms = time_plain_steps(P, lat, stream)
+        kern_ms, kern_direct_ms = time_plain_steps(P, lat, stream)
         # the same kernel with 64-bit element offsets, for comparison
         lat.set_launch(block=lat.get_launch()["block"], offsets32=0)
-        kern64_ms = time_plain_steps(P, lat, stream)
+        kern64_ms, _ = time_plain_steps(P, lat, stream)
         lat.set_launch(block=lat.get_launch()["block"], offsets32=1)
         sb = 2 if prec == P.MFC_FP16_DEV else 4
         byt = step_bytes(w.dim, sb, fo, ao, aq)
         ach = byt / (kern_ms * 1e-3) / 1e9
         out[name] = {"mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
-                     "kernel_ms": kern_ms, "kernel_ms_offsets64": kern64_ms,
+                     "kernel_ms": kern_ms, "kernel_ms_direct": kern_direct_ms,
+                     "kernel_ms_offsets64": kern64_ms,
                      "algorithmic_bytes_per_launch": byt,
                      "achieved_gbs": ach, "roofline_frac": ach / peak,
                      "bytes_per_node": byt / w.nodes}
@@ -838,7 +849,7 @@ def main():
     value = aggregate_mlups(w.nodes, world, args.steps, ms * 1e-3)
 
     # dominant kernel: the plain fused step, timed alone on the same stream
-    kern_ms = time_plain_steps(P, lat, stream)
+    kern_ms, kern_direct_ms = time_plain_steps(P, lat, stream)
     # the same kernel inside the timed region: its share of the step (the rest is the check
     # step, the two sum kernels and the host round trip of each block)
     sb = 2 if prec == P.MFC_FP16_DEV else 4
@@ -932,6 +943,10 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel": kname, "kernel_ms": kern_ms,
+                         "kernel_ms_timing": "mean step of a 400-step CUDA graph as mfc_solve_steady "
+                                             "runs it (398 plain, 1 field-storing, 1 check step): an "
+                                             "upper bound on the plain launch",
+                         "kernel_ms_direct": kern_direct_ms,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS",
