@@ -131,7 +131,7 @@ def measured_peaks():
 
 
 class _Nvml:
-    """Read-only NVML queries through ctypes (the driver's libnvidia-ml): SM clock, its maximum,
+    """Read-only NVML queries through ctypes (libnvidia-ml of the installed NVIDIA driver): SM clock, its maximum,
     power draw and the active clock-event reasons of one GPU, named by UUID."""
 
     SM = 1  # NVML_CLOCK_SM

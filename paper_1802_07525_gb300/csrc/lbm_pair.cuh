@@ -267,9 +267,11 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
     }
 }
 
-// Plain coupled step, two rows per thread: grid (row / block, ceil(ny / 2), nz).  (A loop over
-// several row pairs per thread, loading the next pair's link words ahead, measured slower at
-// every depth tried.)
+// Plain coupled step, two rows per thread: grid (row / block, ceil(ny / 2), nz).  Both
+// dimensions take the reader-side boundary form (tiles that touch no open boundary run code with
+// no boundary handling): 3-D 109.9 against 117.6 us in the writer form.
+// (A loop over several row pairs per thread, loading the next pair's link words ahead, measured
+// slower at every depth tried.)
 template <int DIM, typename ST, int SINK>
 __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_kernel(const StepArgs<DIM, ST> a)
 {
@@ -281,16 +283,12 @@ __global__ void __launch_bounds__(256, PairOccupancy<DIM, ST>::blocks) lbm_pair_
     const int z = DIM == 3 ? (blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1) : 0;
     uint32_t L[2];
     pair_links(a, x, y, z, L);
-    if constexpr (ReaderBoundaries<DIM, ST>::step) {
-        const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
-        if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
-            tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
-            step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z, L);
-        else
-            step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z, L);
-    } else {
-        step_pair<DIM, ST, B_WRITER, SINK>(a, x0, y, z, L);
-    }
+    const int y1 = y + 1 < a.geo.ny ? y + 1 : y;
+    if (tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y, z) ||
+        tile_on_open_boundary<DIM>(a.geo, a.bc, x0, blockDim.x, y1, z))
+        step_pair<DIM, ST, B_BOUNDARY, SINK>(a, x0, y, z, L);
+    else
+        step_pair<DIM, ST, B_INTERIOR, SINK>(a, x0, y, z, L);
 }
 
 }  // namespace mfc

@@ -5,7 +5,7 @@ halo interface as the library's lattices: pull streaming, an inlet and an outlet
 the whole domain, cut faces between slabs).  Stepped through DistributedSlab, with its halo
 exchange and the FP64 all-reduce of the check sums, the two slabs must reproduce the whole
 domain stepped alone, exactly, and the summed check sums and residuals must be the whole
-domain's.  No GPU is involved: this covers the driver's ordering and reductions on two
+domain's.  No GPU is involved: this covers the slab driver's ordering and reductions on two
 processes; the kernels' side is covered on one GPU with slabs in one process.
 """
 import ctypes
