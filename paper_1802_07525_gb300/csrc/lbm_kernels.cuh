@@ -435,12 +435,16 @@ struct StepOccupancy {
 //     when it gathers, boundary nodes write only periodic images and the flow outlet values, and
 //     tiles that touch no open boundary run a second code path with no boundary handling at all.
 // Measured on GB300: the reader-side form makes the batch step 20% and the FP16 2-D step 6-7%
-// faster; the FP32 2-D step (32 registers) and the FP16 3-D step run faster in the writer form.
+// faster; the FP32 2-D step (32 registers) runs faster in the writer form.  All steps of one
+// lattice must take the same form: a writer-side step pulls inlet and transport-outlet values
+// from ghost cells that only a writer-side step before it fills.  FP16 storage takes the reader
+// form in 2-D and 3-D, because its plain steps (two rows per thread) are fastest in it; its
+// single-node steps (check, stored-field and 64-bit-offset steps) follow.
 enum : int { B_WRITER = 0, B_BOUNDARY = 1, B_INTERIOR = 2 };
 template <int DIM, typename ST, int AQ = default_aq<DIM>()> struct ReaderBoundaries {
     // the single-lattice step kernel; D2Q9 transport keeps writer-side ghosts, whose outlet
     // values along the diagonals come from the neighbouring row
-    static constexpr bool step = DIM == 2 && sizeof(ST) == 2 && AQ == 5;
+    static constexpr bool step = sizeof(ST) == 2 && AQ == default_aq<DIM>();
 };
 
 // One step of node (x0 + threadIdx.x, y, z) of one lattice, in a tile of blockDim.x nodes from

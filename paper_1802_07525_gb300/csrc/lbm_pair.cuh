@@ -77,9 +77,11 @@ __device__ __forceinline__ float2 p_store(__half *p0, __half *p1, bool has1, flo
     return __half22float2(h);
 }
 
-// Which plain steps run in pairs (chosen per kernel by measurement).
+// Which plain steps run in pairs (chosen per kernel by measurement).  They must be the ones
+// whose single-node steps take the reader-side boundary form.
 template <int DIM, typename ST> struct PairedStep {
     static constexpr bool value = std::is_same<ST, __half>::value;
+    static_assert(!value || ReaderBoundaries<DIM, ST>::step, "paired and single-node steps share one boundary form");
 };
 
 // Resident blocks of 256 threads per SM: 3-D pairs hold 2 x 19 flow populations at once (80
@@ -269,7 +271,9 @@ __device__ __forceinline__ void step_pair(const StepArgs<DIM, ST> &a, int x0, in
 
 // Plain coupled step, two rows per thread: grid (row / block, ceil(ny / 2), nz).  Both
 // dimensions take the reader-side boundary form (tiles that touch no open boundary run code with
-// no boundary handling): 3-D 109.9 against 117.6 us in the writer form.
+// no boundary handling): 3-D 109.9 against 117.6 us in the writer form.  The single-node steps
+// of the same storage type take it too (ReaderBoundaries), so that the forms never mix on one
+// lattice.
 // (A loop over several row pairs per thread, loading the next pair's link words ahead, measured
 // slower at every depth tried.)
 template <int DIM, typename ST, int SINK>

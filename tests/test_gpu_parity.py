@@ -452,8 +452,29 @@ def test_paired_plain_steps_agree_with_single_node_steps(P, shape, bc, k_half):
             pa, pb = a.read_populations(which), b.read_populations(which)
             tol = rel * np.abs(pb).max() + 1e-7 if rel else 2e-3
             assert maxabs(pa, pb) <= tol, (n, which, maxabs(pa, pb), tol)
+    # solve blocks: paired plain steps between single-node stored-field and check steps (the two
+    # kernels must leave each other the ghost values they read) against single-node steps only
+    for g in lats:
+        g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=60, check_every=10)
+    for which in (P.MFC_POP_FLOW, P.MFC_POP_ADE):
+        pa, pb = a.read_populations(which), b.read_populations(which)
+        assert maxabs(pa, pb) <= 2e-3, ("solve blocks", which, maxabs(pa, pb))
     for g in lats:
         g.close()
+
+
+def test_fp16_3d_solve_blocks_against_oracle(P):
+    """FP16 storage on a 3-D electrode with an inlet and an outlet along z: 200 steps as
+    mfc_solve_steady runs them (paired plain steps, a stored-field and a check step every 20)
+    against 200 steps of the FP64 oracle, within the FP16 bound of the launch-variant test."""
+    w = mi.electrode_3d(20, 16, 24, seed=21)
+    g, o = pair(P, w.shape, w.cls, precision=P.MFC_FP16_DEV, **channel_kw(w))
+    g.solve_steady(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=200, check_every=20)
+    o.step_coupled(200)
+    ef = maxabs(g.read_populations(P.MFC_POP_FLOW), o.f)
+    eg = maxabs(g.read_populations(P.MFC_POP_ADE), o.g)
+    print(f"FP16 3-D, 200 steps in solve blocks: max |df| {ef:.2e}, max |dg| {eg:.2e}")
+    assert ef < 2e-3 and eg < 2e-3, (ef, eg)
 
 
 # ------------------------------------------------------------------------------------------
