@@ -442,9 +442,9 @@ def traffic_record(kernel):
 def time_plain_steps(P, lat, stream, M=400):
     """Average duration of the plain fused step kernel, in ms, two ways, each bracketed by CUDA
     events on the lattice stream: (1) launched as mfc_solve_steady launches it, one CUDA graph of
-    M steps (M - 2 plain steps, one that stores the fields, one check step), the block's time over
-    M: an upper bound on the plain launch's duration, since the other two steps take longer;
-    (2) M direct launches (mfc_step_coupled), which adds each launch's gap."""
+    M steps (M - 1 plain steps and one check step, then the two sum kernels), the block's time
+    over M: an upper bound on the plain launch's duration, since the rest takes longer than a
+    plain step; (2) M direct launches (mfc_step_coupled), which adds each launch's gap."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     solve = dict(mode=P.MFC_CONCURRENT, tol_flow=0.0, tol_ade=0.0, max_steps=M, check_every=M)
@@ -944,8 +944,8 @@ def main():
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel": kname, "kernel_ms": kern_ms,
                          "kernel_ms_timing": "mean step of a 400-step CUDA graph as mfc_solve_steady "
-                                             "runs it (398 plain, 1 field-storing, 1 check step): an "
-                                             "upper bound on the plain launch",
+                                             "runs it (399 plain steps, 1 check step, 2 sum kernels): "
+                                             "an upper bound on the plain launch",
                          "kernel_ms_direct": kern_direct_ms,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,

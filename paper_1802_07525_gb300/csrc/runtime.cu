@@ -4,8 +4,9 @@
 // (pull scheme: read one, write the other), one link word per node, the node classes, the
 // FP32 fields (rho - 1, u, C - c_ref) written on check steps, per-block FP64 partial sums and
 // the finalized results (mirrored into pinned host memory).  Steady solves replay a captured
-// CUDA graph of K steps (K-2 plain, one that stores the fields, one that compares against them
-// and reduces), then read the residuals from the pinned mirror.
+// CUDA graph of K steps (K-1 plain, then one check step that compares the fields with those the
+// previous check stored, stores them and reduces), then read the residuals from the pinned
+// mirror.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
