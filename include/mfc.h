@@ -335,13 +335,16 @@ MFC_API mfc_status mfc_synchronize(mfc_lattice *lat);
 
 /* ---- launch variants ---------------------------------------------------------------------- */
 
-/* How the step kernel is launched: one thread per node, `block` (128 or 256) threads along a
- * row per block.  Every choice computes the same arithmetic. */
+/* How the step kernel is launched: `block` (128 or 256) threads along a row per block, one node
+ * per thread (with FP16 storage and 32-bit offsets, plain coupled steps take two rows per thread,
+ * nodes (x, y) and (x, y + 1), with paired FP32 arithmetic).  Every choice computes the same
+ * arithmetic; the paired form groups the FP32 operations differently, so it agrees to FP32
+ * rounding. */
 typedef struct {
     int block;
     int offsets32;  /* 1 (default): the plain step forms its element offsets in 32 bits where every
                        population array has fewer than 2^31 elements (one multiply-add per address);
-                       0: 64-bit offsets always */
+                       0: 64-bit offsets always, one node per thread */
 } mfc_launch;
 
 /* Select the launch shape (waits for queued work; captured step graphs are rebuilt). */
