@@ -83,6 +83,25 @@ def test_slabs_compute_what_the_whole_lattice_computes(P, name, bc, nslab):
         g.close()
 
 
+@pytest.mark.parametrize("name,bc,nslab", [("anode_2d", (2, 0), 2), ("electrode_3d", (0, 0, 2), 3)])
+def test_fp16_slabs_compute_what_the_whole_lattice_computes(P, name, bc, nslab):
+    """FP16 storage: plain steps two rows per thread, rows paired along y, which no cut divides;
+    the halos carry the stored FP16 values.  Populations bit for bit."""
+    w = mi.anode_2d(150, 40, seed=12) if name == "anode_2d" else mi.electrode_3d(20, 16, 36, seed=13)
+    kw = dict(tau=w.tau, tau_c=w.tau_c, u_in=w.u_in, c_in=w.c_in, k_sink=w.k_sink)
+    whole, slabs, local = split(P, w, nslab, bc, precision=P.MFC_FP16_DEV, **kw)
+    done = 0
+    for target in (1, 7, 150):
+        local.step(target - done)
+        whole.step_coupled_plain(target - done)
+        done = target
+        for which in (P.MFC_POP_FLOW, P.MFC_POP_ADE):
+            a, b = joined(P, w, slabs, which), whole.read_populations(which)
+            assert np.array_equal(a, b), (target, which, float(np.abs(a - b).max()))
+    for g in slabs + [whole]:
+        g.close()
+
+
 def test_slab_steady_solve_matches_the_whole_lattice(P):
     from paper_1802_07525_gb300 import slab as S
     w = mi.electrode_3d(16, 16, 24, seed=9)
